@@ -1,0 +1,334 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each check is chosen so that a plausible slip in the oracle (a dropped
+strictness test, a swapped operand, a row sum instead of a column sum, an
+off-by-one in l, a wrong Philox constant, a wrong pivot rule...) fails here:
+
+* Philox-4x32-10 against the library implementation shipped with Triton
+  (run in its CPU interpreter).
+* Dominance on the full grid {0..q-1}^m against the closed-form pair count
+  (q(q+1)/2)^m - q^m and the per-point count prod_k (q - a_k) - 1.
+* Ranks on the full grid equal sum_k a_k (longest chain from the origin);
+  Deb's sort (Algorithm S.2), the peel (Algorithm S.3) and a longest-chain
+  dynamic programme agree on random inputs with ties.
+* Front points with sum f = 0.5 or ||f|| = 1 form one front.
+* Intercepts equal alpha for corner points z + alpha_k e_k; the linear front
+  gives a = 0.5; a doubled extreme point forces the nadir fallback.
+* A point s R_j associates to j with distance 0; adding delta u with u
+  orthogonal to R_j gives distance delta ||u||.
+* Niching equals a literal one-pick-at-a-time run of Algorithm S.1 that
+  breaks ties by the same random priorities.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_20286_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------- Philox
+def test_philox_matches_triton_library():
+    # the interpreter flag must be set before triton is first imported
+    os.environ["TRITON_INTERPRET"] = "1"
+    pytest.importorskip("triton")
+    from tests import _triton_philox
+
+    n = 64
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    key[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    key[1] = 0xFFFFFFFF
+    ref = _triton_philox.philox(ctr, key)
+    mine = np.stack([oracle.philox4x32_10(ctr[i], key[i]) for i in range(n)])
+    assert np.array_equal(mine, ref)
+
+
+# ------------------------------------------------------------------ dominance
+def grid(q, m):
+    return np.array(list(itertools.product(range(q), repeat=m)), dtype=np.float32)
+
+
+@pytest.mark.parametrize("q,m", [(3, 2), (3, 3), (4, 2), (2, 4)])
+def test_dominance_grid_closed_forms(q, m):
+    F = grid(q, m)
+    n = F.shape[0]
+    D = oracle.dominance_bits(F)
+    bits = np.unpackbits(D.view(np.uint8), bitorder="little").reshape(n, -1)[:, :n]
+    # total number of dominance pairs: coordinatewise <= pairs minus equal pairs
+    assert bits.sum() == (q * (q + 1) // 2) ** m - q ** m
+    # minimisation: point a dominates exactly prod(q - a_k) - 1 grid points
+    for i in range(n):
+        assert bits[i].sum() == int(np.prod(q - F[i])) - 1
+    # never reflexive, never both ways
+    assert not np.any(np.diag(bits))
+    assert not np.any(bits & bits.T)
+    # column sums are the dominator counts: prod(a_k + 1) - 1
+    c = oracle.domination_counts(F)
+    assert np.array_equal(c, (np.prod(F + 1, axis=1) - 1).astype(np.int32))
+    assert np.array_equal(c, bits.sum(axis=0))
+
+
+def test_dominance_direction_and_duplicates():
+    assert oracle.dominates([0.0, 0.0], [1.0, 1.0])
+    assert not oracle.dominates([1.0, 1.0], [0.0, 0.0])
+    assert oracle.dominates([0.0, 1.0], [0.0, 2.0])
+    assert not oracle.dominates([1.0, 1.0], [1.0, 1.0])       # identical points
+    assert not oracle.dominates([0.0, 2.0], [1.0, 1.0])       # incomparable
+    assert not oracle.dominates([-0.0, 1.0], [0.0, 1.0])      # -0 == +0
+
+
+# ------------------------------------------------------------------- ranks
+def longest_chain_ranks(F):
+    """Rank = length of the longest dominance chain ending at the point."""
+    F = F.astype(np.float64)
+    le = np.all(F[:, None, :] <= F[None, :, :], axis=2)
+    lt = np.any(F[:, None, :] < F[None, :, :], axis=2)
+    dom = le & lt
+    n = F.shape[0]
+    rank = np.zeros(n, dtype=np.int64)
+    for _ in range(n):
+        cand = np.where(dom, rank[:, None] + 1, 0).max(axis=0)
+        new = np.maximum(rank, cand)
+        if np.array_equal(new, rank):
+            break
+        rank = new
+    return rank.astype(np.int32)
+
+
+@pytest.mark.parametrize("q,m", [(3, 2), (4, 3), (3, 4)])
+def test_grid_ranks_are_coordinate_sums(q, m):
+    F = grid(q, m)
+    expect = F.sum(axis=1).astype(np.int32)
+    assert np.array_equal(oracle.nd_sort_deb(F), expect)
+    assert np.array_equal(oracle.nd_sort_peel(F), expect)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sorts_agree_with_longest_chain(seed):
+    rng = np.random.default_rng(seed)
+    m = int(rng.integers(2, 6))
+    n = int(rng.integers(2, 90))
+    F = rng.integers(0, 4, size=(n, m)).astype(np.float32)   # many ties/duplicates
+    ref = longest_chain_ranks(F)
+    assert np.array_equal(oracle.nd_sort_deb(F), ref)
+    assert np.array_equal(oracle.nd_sort_peel(F), ref)
+
+
+def test_exhaustive_tiny_populations():
+    # every population of 4 points in {0,1,2}^2 (6561 populations)
+    pts = grid(3, 2)
+    for combo in itertools.product(range(9), repeat=4):
+        F = pts[list(combo)]
+        ref = longest_chain_ranks(F)
+        assert np.array_equal(oracle.nd_sort_deb(F), ref), combo
+
+
+@pytest.mark.parametrize("shape,m", [("linear", 3), ("sphere", 3), ("sphere", 5), ("linear", 8)])
+def test_front_points_form_one_front(shape, m):
+    F = wl.front_points(300, m, shape, seed=11)
+    if shape == "linear":
+        assert np.allclose(F.astype(np.float64).sum(1), 0.5, atol=1e-6)
+    else:
+        assert np.allclose(np.linalg.norm(F.astype(np.float64), axis=1), 1.0, atol=1e-6)
+    r = oracle.nd_sort_deb(F)
+    # float32 rounding can put two nearly identical points in a dominance
+    # relation; check against the brute-force chain and that front 0 holds
+    # almost everything
+    assert np.array_equal(r, longest_chain_ranks(F))
+    assert (r == 0).mean() > 0.97
+
+
+# ---------------------------------------------------------------- selection
+def test_das_dennis_counts():
+    # closed form C(H+M-1, M-1); values of the five workloads
+    assert wl.das_dennis(12, 3).shape[0] == 91
+    assert wl.das_dennis(140, 3).shape[0] == 10011
+    assert wl.das_dennis_two_layer(3, 2, 8).shape[0] == 156
+    assert wl.das_dennis_count(631, 3) == 200028
+    for h, m in [(4, 3), (5, 4), (3, 6)]:
+        R = wl.das_dennis(h, m)
+        assert R.shape[0] == math.comb(h + m - 1, m - 1)
+        assert np.allclose(R.astype(np.float64).sum(1), 1.0, atol=1e-6)
+        assert len({tuple(r) for r in R.tolist()}) == R.shape[0]
+
+
+def check_selection_invariants(F, R, n_keep, surv, t):
+    n2 = F.shape[0]
+    rank = t["rank"]
+    l = t["last_rank"]
+    assert len(surv) == n_keep
+    assert np.all(np.diff(surv) > 0)
+    P = np.flatnonzero(rank < l)
+    L = np.flatnonzero(rank == l)
+    assert len(P) == t["n_before"] and len(L) == t["n_last"]
+    assert len(P) < n_keep <= len(P) + len(L)
+    assert np.sort(rank)[n_keep - 1] == l
+    assert set(P.tolist()) <= set(surv.tolist())
+    extra = sorted(set(surv.tolist()) - set(P.tolist()))
+    assert set(extra) <= set(L.tolist())
+    assert np.array_equal(np.flatnonzero(t["picked"]), np.array(extra, dtype=np.int64))
+    S = rank <= l
+    # ideal point = column minima of S = column minima of front 0
+    assert np.array_equal(t["z"], F[S].astype(np.float64).min(0))
+    assert np.array_equal(t["z"], F[rank == 0].astype(np.float64).min(0))
+    # association outside S is undefined, inside it is a valid index
+    assert np.all(t["pi"][~S] == -1) and np.all((t["pi"][S] >= 0) & (t["pi"][S] < R.shape[0]))
+    # rho counts P members per reference
+    assert np.array_equal(t["rho"], np.bincount(t["pi"][P], minlength=R.shape[0]).astype(np.int32))
+
+
+@pytest.mark.parametrize("cfg_seed", range(4))
+def test_selection_invariants_small(cfg_seed):
+    F = wl.population(184, 3, 7, "linear", seed=100 + cfg_seed)
+    R = wl.das_dennis(12, 3)
+    surv, t = oracle.nsga3_select(F, R, 92, seed=5, generation=cfg_seed)
+    check_selection_invariants(F, R, 92, surv, t)
+    assert np.array_equal(t["rank"], longest_chain_ranks(F))
+
+
+def test_intercepts_corner_points():
+    rng = np.random.default_rng(3)
+    alpha = np.array([0.5, 2.0, 4.0], dtype=np.float64)
+    z = np.array([0.25, 1.0, -0.5])
+    corners = z + np.diag(alpha)
+    interior = z + rng.uniform(0.05, 0.45, size=(40, 3)) * alpha
+    F = np.vstack([interior[:20], corners, interior[20:]]).astype(np.float32)
+    R = wl.das_dennis(4, 3)
+    surv, t = oracle.nsga3_select(F, R, 30, seed=1)
+    assert np.array_equal(t["z"], z)
+    assert list(t["extreme"]) == [20, 21, 22]
+    assert t["fallback"] == 0
+    np.testing.assert_allclose(t["a"], alpha, rtol=1e-14)
+    # normalised corners sit on the axes at 1
+    S = t["rank"] <= t["last_rank"]
+    assert np.all(S[20:23])
+    np.testing.assert_allclose(t["fnorm"][20:23], np.eye(3), atol=1e-15)
+
+
+def test_intercepts_linear_front():
+    F = wl.front_points(200, 3, "linear", seed=4).astype(np.float64)
+    F = np.vstack([np.eye(3) * 0.5, F]).astype(np.float32)
+    surv, t = oracle.nsga3_select(F, wl.das_dennis(6, 3), 100, seed=2)
+    assert t["fallback"] == 0
+    assert np.array_equal(t["z"], np.zeros(3))
+    np.testing.assert_allclose(t["a"], [0.5, 0.5, 0.5], rtol=1e-12)
+
+
+def test_intercepts_degenerate_fallback_to_nadir():
+    F = wl.population(400, 4, 13, "sphere", seed=21)
+    G = wl.ideal_corner_case(F)
+    surv, t = oracle.nsga3_select(G, wl.das_dennis(4, 4), 200, seed=3)
+    assert t["extreme"][0] == t["extreme"][1] == 0
+    assert t["fallback"] == 1
+    S = t["rank"] <= t["last_rank"]
+    nadir = (G[S].astype(np.float64) - t["z"]).max(0)
+    assert np.array_equal(t["a"], nadir)
+
+
+def test_association_closed_forms():
+    # points on reference lines and at known offsets from them
+    R = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]], dtype=np.float32)
+    corners = np.eye(3, dtype=np.float32)
+    on_line = np.array([[0.25, 0.25, 0.25], [0.5, 0.5, 0.5]], dtype=np.float32)
+    u = np.array([1.0, -1.0, 0.0])           # orthogonal to (1,1,1)
+    delta = 0.0625
+    off = (np.array([0.375, 0.375, 0.375]) + delta * u).astype(np.float32)
+    F = np.vstack([corners, on_line, off[None]]).astype(np.float32)
+    surv, t = oracle.nsga3_select(F, R, F.shape[0], seed=0)
+    # z = 0, corners give a = 1, so f' = F
+    assert np.array_equal(t["a"], [1.0, 1.0, 1.0])
+    assert list(t["pi"][:3]) == [0, 1, 2]
+    assert list(t["pi"][3:]) == [3, 3, 3]
+    assert np.all(t["dist"][:5] == 0.0)
+    np.testing.assert_allclose(t["dist"][5], delta * np.linalg.norm(u), rtol=1e-15)
+
+
+def test_keep_whole_last_front_selects_it_all():
+    F = wl.population(120, 3, 8, "sphere", seed=9)
+    r = oracle.nd_sort_deb(F)
+    sizes = np.bincount(r)
+    n_keep = int(sizes[:3].sum())                   # exactly fills fronts 0..2
+    surv, t = oracle.nsga3_select(F, wl.das_dennis(5, 3), n_keep, seed=4)
+    assert t["last_rank"] == 2
+    assert np.array_equal(surv, np.flatnonzero(r <= 2))
+
+
+def niche_random(seed, gen, j, c, tag):
+    ctr = [j & 0xFFFFFFFF, (2 * c + tag) & 0xFFFFFFFF, gen & 0xFFFFFFFF, gen >> 32]
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    return int(oracle.philox4x32_10(ctr, key)[0])
+
+
+def sequential_s1(t, n_r, n_keep, seed, gen):
+    """Algorithm S.1, one pick per iteration: least-crowded live reference
+    (ties by the random priority of the current crowding), nearest member
+    when it has no member yet, otherwise a random member."""
+    rank, pi, dist = t["rank"], t["pi"], t["dist"]
+    l = t["last_rank"]
+    rho = np.bincount(pi[rank < l], minlength=n_r).astype(np.int64)
+    C = {j: [] for j in range(n_r)}
+    for i in np.flatnonzero(rank == l):
+        C[int(pi[i])].append(int(i))
+    live = {j for j in range(n_r) if C[j]}
+    need = n_keep - int((rank < l).sum())
+    picked = []
+    while need > 0:
+        cmin = min(rho[j] for j in live)
+        ties = [j for j in live if rho[j] == cmin]
+        j = min(ties, key=lambda q: (niche_random(seed, gen, q, cmin, 0), q))
+        if rho[j] == 0:
+            a = min(C[j], key=lambda i: (dist[i], i))
+        else:
+            u = niche_random(seed, gen, j, int(rho[j]), 1)
+            a = C[j][(u * len(C[j])) >> 32]
+        C[j].remove(a)
+        picked.append(a)
+        rho[j] += 1
+        need -= 1
+        if not C[j]:
+            live.discard(j)
+    return sorted(picked)
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_niching_equals_sequential_algorithm_s1(case):
+    rng = np.random.default_rng(50 + case)
+    m = int(rng.integers(2, 5))
+    n2 = int(rng.integers(40, 260))
+    shape = "linear" if case % 2 else "sphere"
+    F = wl.population(n2, m, m + 4, shape, seed=77 + case)
+    if case >= 6:
+        F = (np.round(F * 8) / 8).astype(np.float32)   # ties and duplicates
+    H = int(rng.integers(2, 7))
+    R = wl.das_dennis(H, m)
+    n_keep = int(rng.integers(1, n2 + 1))
+    seed, gen = int(rng.integers(0, 2 ** 63)), int(rng.integers(0, 2 ** 40))
+    surv, t = oracle.nsga3_select(F, R, n_keep, seed=seed, generation=gen)
+    check_selection_invariants(F, R, n_keep, surv, t)
+    assert np.flatnonzero(t["picked"]).tolist() == sequential_s1(t, R.shape[0], n_keep, seed, gen)
+
+
+def test_golden_config0():
+    """Regression fixture written by tests/golden/make_golden.py (oracle only)."""
+    path = os.path.join(GOLDEN, "config0_oracle.txt")
+    gold = {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split(":", 1)
+            gold[k.strip()] = v.strip()
+    p = wl.config(0)
+    surv, t = oracle.nsga3_select(p.F, p.R, p.n_keep, p.seed, p.generation)
+    assert " ".join(map(str, surv.tolist())) == gold["survivors"]
+    assert " ".join(map(str, t["rank"].tolist())) == gold["rank"]
+    assert int(gold["last_rank"]) == t["last_rank"]
