@@ -1,0 +1,304 @@
+#!/usr/bin/env python3
+"""Throughput of NSGA-III environmental selection on GB300.
+
+Workload: one merged population of 2N = 400,000 points with M = 3 float32
+objectives (sphere-front stand-in, D = 12 decision variables) and 200,028
+Das-Dennis directions (H = 631), keeping N = 200,000. One step is one full
+``emo_nsga3_select`` call (ordering, dominance, peeling, normalisation,
+association, niching, survivors) with the inputs resident in HBM.
+
+Prints one JSON line. ``value`` is dominance pairs (2N)^2 per second through
+whole selection steps, summed over ranks (weak scaling: every rank selects
+its own population, no collective on the data path). ``--impl reference``
+times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dominance pairs/s and selections/s at 2N=400k; batched vs plain; % of roofline"
+UNIT = "pairs/s"
+N2, M, H, D_VARS = 400_000, 3, 631, 12
+SAMPLE_N2, SAMPLE_H = 16_000, 126        # oracle sample: first 16,000 points, 8,128 directions
+FLUSH_BYTES = 512 << 20                   # > 129 MB L2
+KERNELS_PER_STEP = 11                     # launches of one single-population selection
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n2", type=int, default=N2, help="population size (default: the 400k workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return {"hbm_gbs": p.get("hbm_gbs", 6800.0), "sm_max_mhz": p.get("sm_max_mhz", 2070.0),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def workload(n2: int, seed_offset: int = 0):
+    from paper_2503_20286_gb300 import workloads as wl
+    seed = wl.BASE_SEED + 4 + seed_offset
+    F = wl.population(n2, M, D_VARS, "sphere", seed)
+    h = H if n2 == N2 else wl.h_for_count(n2 // 2, M)
+    R = wl.das_dennis(h, M)
+    return F, R, n2 // 2, seed
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_time(F, R, n_keep, seed, sample_n2: int):
+    """FP64 CPU oracle on the first `sample_n2` points (same distribution)."""
+    import oracle
+    from paper_2503_20286_gb300 import workloads as wl
+    oracle.build()
+    Fs = np.ascontiguousarray(F[:sample_n2])
+    Rs = wl.das_dennis(SAMPLE_H, M) if sample_n2 == SAMPLE_N2 else wl.das_dennis(
+        wl.h_for_count(sample_n2 // 2, M), M)
+    t0 = time.perf_counter()
+    oracle.nsga3_select(Fs, Rs, sample_n2 // 2, seed, 0, trace=False)
+    dt = time.perf_counter() - t0
+    return dt, Rs.shape[0]
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    F, R, n_keep, seed = workload(args.n2)
+    ts = []
+    for i in range(args.warmup + args.steps):
+        dt, nr_s = oracle_time(F, R, n_keep, seed, SAMPLE_N2)
+        if i >= args.warmup:
+            ts.append(dt)
+    t = statistics.mean(ts)
+    value = SAMPLE_N2 ** 2 / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"NSGA-III selection, sample 2N={SAMPLE_N2} of the 2N={args.n2} M={M} "
+                                   f"sphere population, {nr_s} directions", "n2": SAMPLE_N2, "m": M},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {SAMPLE_N2} points of the workload, {nr_s} Das-Dennis directions, "
+                                       f"keep {SAMPLE_N2 // 2}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2503_20286_gb300 import build as emo_build
+    from paper_2503_20286_gb300 import _binding as emo
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or not os.path.exists(emo_build.LIB):
+        emo_build.build()
+    if world > 1:
+        dist.barrier()
+    emo.lib()
+
+    F, R, n_keep, seed = workload(args.n2, seed_offset=rank)
+    n2, n_r = F.shape[0], R.shape[0]
+    Ft = torch.from_numpy(F).to(dev)
+    Rt = torch.from_numpy(R).to(dev)
+    surv = torch.empty(n_keep, dtype=torch.int32, device=dev)
+    info = torch.zeros(8, dtype=torch.int32, device=dev)
+    ws_bytes = emo.emo_workspace_size(emo.EMO_OP_NSGA3_SELECT, n2, M, n_r)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(gen):
+        emo.emo_nsga3_select(Ft, Rt, n_keep, seed, gen, survivors=surv, info=info, ws=ws)
+
+    for w in range(args.warmup):
+        step(w)
+    torch.cuda.synchronize()
+    st = emo.emo_workspace_status(ws)
+    if st != 0:
+        raise SystemExit(f"selection failed on the device: status {st}")
+
+    emo.emo_set_stage_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_ms: dict[str, list[float]] = {}
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step(args.warmup + k)
+        ev[k][1].record(stream)
+        for name, ms in emo.emo_stage_times():
+            stage_ms.setdefault(name, []).append(ms)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    emo.emo_set_stage_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = emo.emo_workspace_status(ws)
+    if st != 0:
+        raise SystemExit(f"selection failed on the device: status {st}")
+    info_h = info.cpu().tolist()
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    F_host = torch.from_numpy(F).pin_memory()
+    R_host = torch.from_numpy(R).pin_memory()
+    S_host = torch.empty(n_keep, dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e_s.record(stream)
+    for k in range(e2e_steps):
+        Ft.copy_(F_host, non_blocking=True)
+        Rt.copy_(R_host, non_blocking=True)
+        step(1000 + k)
+        S_host.copy_(surv, non_blocking=True)
+    e_e.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e_s.elapsed_time(e_e) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    pairs = float(n2) * float(n2)
+    ms_per_step = total_ms / args.steps
+    value = world * pairs * args.steps / (total_ms / 1e3)
+    pk = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    dom_ms = statistics.mean(stage_ms.get("dominance", [float("nan")]))
+    # dominance roofline: the triangle kernel issues (M-1) compares and one
+    # bit insert per unordered pair, against SMs x 128 lanes x max SM clock
+    dom_ops = n2 * (n2 - 1) / 2 * M
+    alu_peak = sms * 128 * pk["sm_max_mhz"] * 1e6
+    achieved = dom_ops / (dom_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"NSGA-III selection 2N={n2} M={M} n_r={n_r} keep {n_keep}, sphere-front "
+                               f"stand-in D={D_VARS}", "n2": n2, "m": M, "n_r": n_r, "n_keep": n_keep,
+                   "l2": f"flushed ({FLUSH_BYTES >> 20} MB write) before every timed step",
+                   "parallelism": f"replicas x{world} (independent populations)"},
+        "selections_per_s": world * 1e3 / ms_per_step,
+        "dominance_pairs_per_s_kernel": pairs / (dom_ms / 1e3),
+        "stage_ms": {k: statistics.mean(v) for k, v in stage_ms.items()},
+        "roofline": {"bound": "alu", "kernel": "k_dom_tri<3>", "achieved": achieved / 1e12,
+                     "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": achieved / alu_peak,
+                     "traffic": None, "peak_source": f"{sms} SMs x 128 lanes x {pk['sm_max_mhz']:.0f} MHz "
+                                                     f"({pk['source']} clock)"},
+        "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(F.nbytes + R.nbytes), "d2h_bytes_per_step": int(n_keep * 4)},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": clk,
+        "info": dict(zip(("status", "last_rank", "n_before", "n_last", "fallback_used", "n_recheck",
+                          "n_fronts", "n_levels"), info_h)),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, nr_s = oracle_time(F, R, n_keep, seed, SAMPLE_N2)
+        line["cpu_baseline"] = {"value": SAMPLE_N2 ** 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {SAMPLE_N2} points of the workload, {nr_s} Das-Dennis "
+                                          f"directions, keep {SAMPLE_N2 // 2}; {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * emo.h -- C ABI of the GB300 (sm_103a) NSGA-III environmental-selection
+ * library (arXiv 2503.20286, "Bridging Evolutionary Multiobjective
+ * Optimization and GPU Acceleration via Tensorization").
+ *
+ * Conventions shared by every entry point:
+ *  - Every array argument is a DEVICE pointer owned by the caller. The
+ *    library never allocates device memory; the multi-stage calls take a
+ *    caller-allocated workspace whose size the *_workspace_size queries give.
+ *    Workspaces must be 256-byte aligned (cudaMalloc / torch allocations are).
+ *  - Objectives are row-major float32: F[i * m + k], i < n2, k < m.
+ *    Reference directions are row-major float32: R[j * m + k], j < n_r.
+ *    Objectives are minimised.
+ *  - Calls are asynchronous and ordered on `stream` (a cudaStream_t; NULL
+ *    is the legacy default stream). Argument errors are returned
+ *    immediately and nothing is launched. Errors found on the device
+ *    (non-finite objectives, a bounded wait that ran out) are written to
+ *    `info->status` when `info` is given, and always to the workspace
+ *    status word read by emo_workspace_status().
+ *  - Several calls may run concurrently on different streams as long as each
+ *    has its own workspace and outputs.
+ */
+#ifndef EMO_H
+#define EMO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* emo_stream_t; /* a cudaStream_t */
+
+typedef enum {
+    EMO_OK = 0,
+    EMO_ERR_INVALID_ARG = 1,     /* bad size, null pointer, misaligned buffer */
+    EMO_ERR_NONFINITE = 2,       /* NaN/Inf in F or R, or a zero reference    */
+    EMO_ERR_WORKSPACE = 3,       /* workspace smaller than required           */
+    EMO_ERR_CUDA = 4,            /* a CUDA runtime call failed                */
+    EMO_ERR_TIMEOUT = 5,         /* a bounded device wait ran out             */
+    EMO_ERR_NOT_IMPLEMENTED = 6
+} emo_status;
+
+/* Upper limits accepted by every entry point. */
+#define EMO_MAX_OBJECTIVES 16
+#define EMO_MAX_BATCH 128
+#define EMO_NOT_RANKED 2147483647 /* rank of points beyond the last needed front */
+
+/* Per-call facts written on the device (all fields int32). */
+typedef struct {
+    int32_t status;        /* emo_status detected on the device            */
+    int32_t last_rank;     /* l: rank of the n_keep-th best point           */
+    int32_t n_before;      /* |P| = #{rank < l}                             */
+    int32_t n_last;        /* |L| = #{rank == l}                            */
+    int32_t fallback_used; /* 1: nadir point replaced the intercepts        */
+    int32_t n_recheck;     /* points associated by an all-reference FP64 scan */
+    int32_t n_fronts;      /* fronts peeled (l + 1 for selection)           */
+    int32_t n_levels;      /* niching levels run                            */
+} emo_select_info;
+
+/* Optional intermediate outputs of emo_nsga3_select_debug (device pointers,
+ * each nullable). Index order is the caller's point order. */
+typedef struct {
+    int32_t* rank;    /* [n2] front index, EMO_NOT_RANKED beyond l          */
+    float* z;         /* [m] ideal point over S = {rank <= l}               */
+    int32_t* extreme; /* [m] index of the ASF extreme point of each axis    */
+    double* a;        /* [m] hyperplane intercepts (after any fallback)     */
+    float* fnorm;     /* [n2*m] normalised objectives, NaN outside S        */
+    int32_t* pi;      /* [n2] associated reference, -1 outside S            */
+    double* dist;     /* [n2] perpendicular distance, NaN outside S         */
+    int32_t* rho;     /* [n_r] niche counts of P = {rank < l}               */
+    uint8_t* picked;  /* [n2] 1 when chosen by niching                      */
+} emo_select_debug;
+
+/* One population of a batched call. */
+typedef struct {
+    const float* F;        /* [n2*m] objectives                              */
+    const float* R;        /* [n_r*m] reference directions                   */
+    int32_t* survivors;    /* [n_keep] output, ascending point indices       */
+    emo_select_info* info; /* nullable                                       */
+    int64_t n2;
+    int64_t n_keep;
+    int32_t m;
+    int32_t n_r;
+    uint64_t seed;
+    uint64_t generation;
+} emo_problem;
+
+typedef enum { EMO_OP_DOMINANCE = 0, EMO_OP_ND_RANK = 1, EMO_OP_NSGA3_SELECT = 2 } emo_op;
+
+/* Bytes of workspace needed by `op` for a population of n2 points with m
+ * objectives and n_r reference directions (n_r ignored for ranking). Returns
+ * 0 when the sizes are out of range. EMO_OP_DOMINANCE needs none. */
+size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r);
+
+/*
+ * Pareto-dominance matrix (Section III-C, Listing 1; Section IV-A "D_ij =
+ * F_i dominates F_j"; Algorithm S.3 first line) and the number of dominators
+ * of each point (Algorithm S.3 second line, read as the column sum).
+ *   F         [n2*m] objectives, 1 <= n2 <= 2^21, 2 <= m <= 16.
+ *   D         [n2*ld_words] uint32 output. Row i, word w, bit b is 1 iff
+ *             F_i dominates F_{32w+b} (all <= and some <). Bits of columns
+ *             >= n2 are zero. ld_words >= ceil(n2/32).
+ *   dom_count [n2] int32 output, nullable: dom_count[j] = sum_i D[i][j].
+ * Comparisons are exact in float32; -0 equals +0.
+ */
+emo_status emo_dominance(const float* F, int64_t n2, int32_t m, uint32_t* D, int64_t ld_words,
+                         int32_t* dom_count, emo_stream_t stream);
+
+/*
+ * Nondominated sorting (Section IV-A "Nondominated Sorting", Algorithm S.3,
+ * equal to Deb's sort of Algorithm S.2).
+ *   n_keep    0 ranks every point; otherwise peeling stops at the first
+ *             front l whose cumulative size reaches n_keep, and points of
+ *             later fronts get EMO_NOT_RANKED.
+ *   rank      [n2] int32 output, 0-based front index.
+ *   last_rank device int32*, nullable: l (rank of the n_keep-th best point;
+ *             the last front when n_keep == 0).
+ *   ws        workspace of emo_workspace_size(EMO_OP_ND_RANK, n2, m, 0) bytes.
+ */
+emo_status emo_nd_rank(const float* F, int64_t n2, int32_t m, int64_t n_keep, int32_t* rank,
+                       int32_t* last_rank, void* ws, size_t ws_bytes, emo_stream_t stream);
+
+/*
+ * NSGA-III environmental selection (Algorithm S.1; tensorized form in
+ * Section IV-A and Algorithm S.4): nondominated sorting, normalisation by
+ * the ideal point, ASF extreme points and hyperplane intercepts with the
+ * nadir fallback (Algorithm S.5; FP64), association to the reference lines
+ * by perpendicular distance, niche counts, and niching of the last front.
+ *   R          [n_r*m] reference directions, finite, non-zero rows.
+ *   n_keep     N, 1 <= N <= n2.
+ *   seed, generation  key and counter of the Philox-4x32-10 stream that
+ *              breaks niching ties (same inputs give the same survivors).
+ *   survivors  [n_keep] int32 output: indices of the survivors, ascending.
+ *   info       device emo_select_info*, nullable.
+ *   ws         workspace of emo_workspace_size(EMO_OP_NSGA3_SELECT, ...)
+ *              bytes; about n2^2/16 bytes for the dominance tiles plus
+ *              O(n2 + n_r) for the rest.
+ */
+emo_status emo_nsga3_select(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
+                            int64_t n_keep, uint64_t seed, uint64_t generation, int32_t* survivors,
+                            emo_select_info* info, void* ws, size_t ws_bytes, emo_stream_t stream);
+
+/* As emo_nsga3_select, also writing the intermediates named in `dbg` (a
+ * host pointer to a struct of device pointers, nullable). */
+emo_status emo_nsga3_select_debug(const float* F, int64_t n2, int32_t m, const float* R,
+                                  int32_t n_r, int64_t n_keep, uint64_t seed, uint64_t generation,
+                                  int32_t* survivors, emo_select_info* info,
+                                  const emo_select_debug* dbg, void* ws, size_t ws_bytes,
+                                  emo_stream_t stream);
+
+/*
+ * Many independent populations (uneven n2, m, n_r) in one sequence of
+ * launches: each stage is one persistent launch that serves every
+ * population, so the whole batch can be captured in one CUDA graph.
+ * Batching is not in the paper; its vmap over populations (Section III-C)
+ * is the analogue. `descs` is a HOST array of `batch` descriptors
+ * (1 <= batch <= EMO_MAX_BATCH) whose pointers are device pointers; it is
+ * read during the call only.
+ */
+size_t emo_batch_workspace_size(const emo_problem* descs, int32_t batch);
+emo_status emo_nsga3_select_batch(const emo_problem* descs, int32_t batch, void* ws,
+                                  size_t ws_bytes, emo_stream_t stream);
+
+/* Synchronises `stream` and reads the device status word of a workspace
+ * last used on it (EMO_OK when every problem finished cleanly). */
+emo_status emo_workspace_status(const void* ws, emo_stream_t stream, int32_t* status_out);
+
+/* Bounded-wait budget (in SM clock cycles) for the device-side barriers of
+ * later calls in this process; 0 restores the default (about 2 s). */
+void emo_set_spin_budget(int64_t cycles);
+
+/* Static description of a status code. */
+const char* emo_status_string(int status);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int32_t emo_version(void);
+
+/* Opt-in stage timing for profiling. While enabled, every multi-stage call
+ * records CUDA events on its stream between its stages (prep, sort,
+ * dominance, peel, stats, assoc, rescan, csr, niche, finish). After a call,
+ * emo_stage_times synchronises on the last event and writes up to max_n
+ * stage durations (ms, host array) and static stage names (host array of
+ * const char*, nullable). Returns the number of stages, 0 when nothing was
+ * recorded on this host thread, -1 on a CUDA error. */
+void emo_set_stage_timing(int32_t enable);
+int32_t emo_stage_times(float* ms_out, const char** names_out, int32_t max_n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMO_H */

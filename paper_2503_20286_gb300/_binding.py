@@ -1,0 +1,263 @@
+"""ctypes binding of ``libemo.so`` (include/emo.h) with torch tensors.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. Functions keep the C names. Tensors must live on the current CUDA
+device; calls are enqueued on ``torch.cuda.current_stream()`` unless a
+stream is given. There is no CPU fallback: a missing or unloadable library
+raises ``EmoLibraryError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+EMO_OK = 0
+STATUS_NAMES = {0: "EMO_OK", 1: "EMO_ERR_INVALID_ARG", 2: "EMO_ERR_NONFINITE", 3: "EMO_ERR_WORKSPACE",
+                4: "EMO_ERR_CUDA", 5: "EMO_ERR_TIMEOUT", 6: "EMO_ERR_NOT_IMPLEMENTED"}
+EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT = 0, 1, 2
+EMO_NOT_RANKED = 2147483647
+EMO_MAX_BATCH = 128
+
+_lock = threading.Lock()
+_lib = None
+
+
+class EmoLibraryError(RuntimeError):
+    pass
+
+
+class EmoError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+class SelectInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("status", "last_rank", "n_before", "n_last", "fallback_used",
+                                               "n_recheck", "n_fronts", "n_levels")]
+
+
+class SelectDebug(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("rank", "z", "extreme", "a", "fnorm", "pi", "dist", "rho",
+                                                "picked")]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_void_p), ("R", ctypes.c_void_p), ("survivors", ctypes.c_void_p),
+                ("info", ctypes.c_void_p), ("n2", ctypes.c_int64), ("n_keep", ctypes.c_int64),
+                ("m", ctypes.c_int32), ("n_r", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("generation", ctypes.c_uint64)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False) -> ctypes.CDLL:
+    """The loaded CUDA library; raises when it is absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise EmoLibraryError(f"{path} is missing: run paper_2503_20286_gb300.build.build()")
+                _build.build()
+            try:
+                L = ctypes.CDLL(path)
+            except OSError as e:
+                raise EmoLibraryError(f"cannot load {path}: {e}") from e
+            vp, i64, i32, u64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_size_t
+            L.emo_workspace_size.restype = sz
+            L.emo_workspace_size.argtypes = [ctypes.c_int, i64, i32, i32]
+            L.emo_dominance.restype = ctypes.c_int
+            L.emo_dominance.argtypes = [vp, i64, i32, vp, i64, vp, vp]
+            L.emo_nd_rank.restype = ctypes.c_int
+            L.emo_nd_rank.argtypes = [vp, i64, i32, i64, vp, vp, vp, sz, vp]
+            L.emo_nsga3_select.restype = ctypes.c_int
+            L.emo_nsga3_select.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp, vp, sz, vp]
+            L.emo_nsga3_select_debug.restype = ctypes.c_int
+            L.emo_nsga3_select_debug.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp,
+                                                 ctypes.POINTER(SelectDebug), vp, sz, vp]
+            L.emo_batch_workspace_size.restype = sz
+            L.emo_batch_workspace_size.argtypes = [ctypes.POINTER(Problem), i32]
+            L.emo_nsga3_select_batch.restype = ctypes.c_int
+            L.emo_nsga3_select_batch.argtypes = [ctypes.POINTER(Problem), i32, vp, sz, vp]
+            L.emo_workspace_status.restype = ctypes.c_int
+            L.emo_workspace_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
+            L.emo_set_spin_budget.restype = None
+            L.emo_set_spin_budget.argtypes = [i64]
+            L.emo_status_string.restype = ctypes.c_char_p
+            L.emo_status_string.argtypes = [ctypes.c_int]
+            L.emo_version.restype = i32
+            L.emo_version.argtypes = []
+            L.emo_set_stage_timing.restype = None
+            L.emo_set_stage_timing.argtypes = [i32]
+            L.emo_stage_times.restype = i32
+            L.emo_stage_times.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p), i32]
+            _lib = L
+        return _lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != EMO_OK:
+        raise EmoError(rc, what)
+
+
+def _ws(nbytes: int, ws, device) -> torch.Tensor:
+    if ws is not None:
+        if ws.numel() * ws.element_size() < nbytes:
+            raise EmoError(3, "workspace")
+        return ws
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def emo_workspace_size(op: int, n2: int, m: int, n_r: int = 0) -> int:
+    return int(lib().emo_workspace_size(op, n2, m, n_r))
+
+
+def emo_dominance(F: torch.Tensor, D: torch.Tensor | None = None, dom_count: torch.Tensor | None = None,
+                  with_count: bool = True, stream=None):
+    """Bit-packed dominance matrix ``D [n2, ld]`` (uint32 stored as int32) and dominator counts."""
+    n2, m = F.shape
+    ld = (n2 + 31) // 32
+    if D is None:
+        D = torch.empty((n2, ld), dtype=torch.int32, device=F.device)
+    if dom_count is None and with_count:
+        dom_count = torch.empty(n2, dtype=torch.int32, device=F.device)
+    _check(lib().emo_dominance(_ptr(F), n2, m, _ptr(D), D.shape[1], _ptr(dom_count), _stream(stream)),
+           "emo_dominance")
+    return D, dom_count
+
+
+def emo_nd_rank(F: torch.Tensor, n_keep: int = 0, rank: torch.Tensor | None = None,
+                last_rank: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    n2, m = F.shape
+    if rank is None:
+        rank = torch.empty(n2, dtype=torch.int32, device=F.device)
+    if last_rank is None:
+        last_rank = torch.empty(1, dtype=torch.int32, device=F.device)
+    nbytes = emo_workspace_size(EMO_OP_ND_RANK, n2, m, 0)
+    if nbytes == 0:
+        raise EmoError(1, "emo_workspace_size")
+    ws = _ws(nbytes, ws, F.device)
+    _check(lib().emo_nd_rank(_ptr(F), n2, m, n_keep, _ptr(rank), _ptr(last_rank), _ptr(ws), nbytes,
+                             _stream(stream)), "emo_nd_rank")
+    return rank, last_rank
+
+
+def emo_nsga3_select(F: torch.Tensor, R: torch.Tensor, n_keep: int, seed: int = 0, generation: int = 0,
+                     survivors: torch.Tensor | None = None, info: torch.Tensor | None = None,
+                     ws: torch.Tensor | None = None, debug: dict | None = None, stream=None):
+    """Survivor indices (ascending, int32 ``[n_keep]``) on the device.
+
+    ``info`` is an int32 tensor of 8 elements (``SelectInfo`` layout);
+    ``debug`` maps names of ``SelectDebug`` fields to device tensors.
+    """
+    n2, m = F.shape
+    n_r = R.shape[0]
+    if survivors is None:
+        survivors = torch.empty(n_keep, dtype=torch.int32, device=F.device)
+    nbytes = emo_workspace_size(EMO_OP_NSGA3_SELECT, n2, m, n_r)
+    if nbytes == 0:
+        raise EmoError(1, "emo_workspace_size")
+    ws = _ws(nbytes, ws, F.device)
+    seed &= 0xFFFFFFFFFFFFFFFF
+    generation &= 0xFFFFFFFFFFFFFFFF
+    if debug:
+        dbg = SelectDebug()
+        for k, t in debug.items():
+            setattr(dbg, k, _ptr(t))
+        rc = lib().emo_nsga3_select_debug(_ptr(F), n2, m, _ptr(R), n_r, n_keep, seed, generation,
+                                          _ptr(survivors), _ptr(info), ctypes.byref(dbg), _ptr(ws), nbytes,
+                                          _stream(stream))
+    else:
+        rc = lib().emo_nsga3_select(_ptr(F), n2, m, _ptr(R), n_r, n_keep, seed, generation, _ptr(survivors),
+                                    _ptr(info), _ptr(ws), nbytes, _stream(stream))
+    _check(rc, "emo_nsga3_select")
+    return survivors
+
+
+def _problems(problems) -> ctypes.Array:
+    arr = (Problem * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i].F = _ptr(p["F"])
+        arr[i].R = _ptr(p["R"])
+        arr[i].survivors = _ptr(p["survivors"])
+        arr[i].info = _ptr(p.get("info"))
+        arr[i].n2 = p["F"].shape[0]
+        arr[i].m = p["F"].shape[1]
+        arr[i].n_r = p["R"].shape[0]
+        arr[i].n_keep = p["n_keep"]
+        arr[i].seed = p.get("seed", 0) & 0xFFFFFFFFFFFFFFFF
+        arr[i].generation = p.get("generation", 0) & 0xFFFFFFFFFFFFFFFF
+    return arr
+
+
+def emo_batch_workspace_size(problems) -> int:
+    arr = _problems(problems)
+    return int(lib().emo_batch_workspace_size(arr, len(problems)))
+
+
+def emo_nsga3_select_batch(problems, ws: torch.Tensor | None = None, stream=None):
+    """``problems``: list of dicts with F, R, n_keep, survivors[, info, seed, generation]."""
+    arr = _problems(problems)
+    nbytes = int(lib().emo_batch_workspace_size(arr, len(problems)))
+    if nbytes == 0:
+        raise EmoError(1, "emo_batch_workspace_size")
+    ws = _ws(nbytes, ws, problems[0]["F"].device)
+    _check(lib().emo_nsga3_select_batch(arr, len(problems), _ptr(ws), nbytes, _stream(stream)),
+           "emo_nsga3_select_batch")
+    return ws
+
+
+def emo_workspace_status(ws: torch.Tensor, stream=None) -> int:
+    out = ctypes.c_int32(0)
+    _check(lib().emo_workspace_status(_ptr(ws), _stream(stream), ctypes.byref(out)), "emo_workspace_status")
+    return int(out.value)
+
+
+def emo_set_spin_budget(cycles: int) -> None:
+    lib().emo_set_spin_budget(int(cycles))
+
+
+def emo_status_string(status: int) -> str:
+    return lib().emo_status_string(int(status)).decode()
+
+
+def emo_version() -> int:
+    return int(lib().emo_version())
+
+
+def emo_set_stage_timing(enable: bool) -> None:
+    lib().emo_set_stage_timing(1 if enable else 0)
+
+
+def emo_stage_times() -> list[tuple[str, float]]:
+    """(stage, ms) of the last multi-stage call on this host thread."""
+    ms = (ctypes.c_float * 16)()
+    names = (ctypes.c_char_p * 16)()
+    n = lib().emo_stage_times(ms, names, 16)
+    if n < 0:
+        raise EmoError(4, "emo_stage_times")
+    return [(names[i].decode(), float(ms[i])) for i in range(n)]

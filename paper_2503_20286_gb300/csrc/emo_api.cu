@@ -1,0 +1,378 @@
+// C ABI entry points (include/emo.h): argument checks, workspace layout and
+// the launch sequence of each call. All device work is stream ordered; no
+// call synchronises except emo_workspace_status.
+#include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "emo_kernels.cuh"
+
+using namespace emo;
+
+namespace {
+
+std::atomic<long long> g_spin_budget{0};
+std::atomic<int> g_timing{0};
+
+// Per-thread stage timing of the last run() (opt-in; events on the launch stream).
+constexpr int kMaxStages = 16;
+struct StageTimes {
+    cudaEvent_t ev[kMaxStages + 1] = {};
+    const char* name[kMaxStages] = {};
+    int n = 0;
+    bool created = false;
+    int dev = -1;
+};
+thread_local StageTimes g_st;
+
+struct StageMarker {
+    bool on;
+    cudaStream_t s;
+    explicit StageMarker(cudaStream_t st) : on(g_timing.load() != 0), s(st)
+    {
+        if (!on) return;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (g_st.created && g_st.dev != dev) {
+            for (auto& e : g_st.ev) cudaEventDestroy(e);
+            g_st.created = false;
+        }
+        if (!g_st.created) {
+            for (auto& e : g_st.ev) cudaEventCreate(&e);
+            g_st.created = true;
+            g_st.dev = dev;
+        }
+        g_st.n = 0;
+        cudaEventRecord(g_st.ev[0], s);
+    }
+    void mark(const char* nm)
+    {
+        if (!on || g_st.n >= kMaxStages) return;
+        g_st.name[g_st.n] = nm;
+        cudaEventRecord(g_st.ev[++g_st.n], s);
+    }
+};
+
+long long spin_budget()
+{
+    long long b = g_spin_budget.load();
+    if (b > 0) return b;
+    static long long env = [] {
+        const char* e = std::getenv("EMO_SPIN_BUDGET");
+        long long v = e ? std::atoll(e) : 0;
+        return v > 0 ? v : 4000000000ll;  // ~2 s at 2 GHz
+    }();
+    return env;
+}
+
+struct DevInfo {
+    int sms = 0;
+    int G = 0;  // CTAs of each cooperative launch
+    bool ok = false;
+};
+
+DevInfo dev_info()
+{
+    static std::mutex mu;
+    static std::vector<DevInfo> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DevInfo{};
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1);
+    DevInfo& di = cache[dev];
+    if (!di.ok) {
+        int sms = 0, coop = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return DevInfo{};
+        if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+            return DevInfo{};
+        int occ = 2;
+        const void* kernels[] = {(const void*)k_sort, (const void*)k_peel, (const void*)k_stats,
+                                 (const void*)k_csr, (const void*)k_finish};
+        for (const void* k : kernels) {
+            int o = 0;
+            // k_peel takes up to 8 KB of dynamic shared memory
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, kCoopThreads, 8192) != cudaSuccess)
+                return DevInfo{};
+            occ = std::min(occ, o);
+        }
+        if (occ < 1) return DevInfo{};
+        di.sms = sms;
+        di.G = sms * occ;
+        di.ok = true;
+    }
+    return di;
+}
+
+constexpr int64_t kPlanBytes = (int64_t)((sizeof(Plan) + 255) / 256 * 256);
+
+bool sizes_ok(int64_t n2, int32_t m) { return n2 >= 1 && n2 <= kMaxN2 && m >= 2 && m <= kMaxM; }
+
+ProbIn make_in(const float* F, const float* R, int64_t n2, int32_t m, int32_t n_r, int64_t n_keep, uint64_t seed,
+               uint64_t gen, int32_t* surv, emo_select_info* info, int mode)
+{
+    ProbIn in;
+    std::memset(&in, 0, sizeof(in));
+    in.F = F;
+    in.R = R;
+    in.survivors = surv;
+    in.info = info;
+    in.n2 = n2;
+    in.n_keep = n_keep;
+    in.m = m;
+    in.n_r = n_r;
+    in.seed = seed;
+    in.gen = gen;
+    in.mode = mode;
+    return in;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+cudaError_t coop(const void* fn, int G, size_t smem, cudaStream_t s, Plan* plan)
+{
+    void* args[] = {&plan};
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCoopThreads), args, smem, s);
+}
+
+// Launch the whole pipeline for problems already laid out in `ins` (ordered
+// by objective count).
+emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t s)
+{
+    DevInfo di = dev_info();
+    if (!di.ok) return EMO_ERR_CUDA;
+    const int nprob = (int)ins.size();
+    if (nprob < 1 || nprob > kMaxBatch || nprob > di.G) return EMO_ERR_INVALID_ARG;
+    if (!ws || !aligned(ws, 256)) return EMO_ERR_INVALID_ARG;
+    int64_t off = kPlanBytes;
+    int max_ncb = 1;
+    bool any_select = false;
+    for (auto& in : ins) {
+        in.ws_off = (uint64_t)off;
+        off += layout_problem(in, di.G, nullptr, nullptr);
+        max_ncb = std::max<int>(max_ncb, (int)cdiv(in.n2, kColBlock));
+        any_select |= in.mode == MODE_SELECT;
+    }
+    if ((int64_t)ws_bytes < off) return EMO_ERR_WORKSPACE;
+
+    static thread_local SetupArgs args;
+    std::memset(&args, 0, sizeof(args));
+    args.nprob = nprob;
+    args.G = di.G;
+    args.spin_budget = spin_budget();
+    for (int p = 0; p < nprob; ++p) args.in[p] = ins[p];
+    Plan* plan = (Plan*)ws;
+    char* base = (char*)ws;
+
+    StageMarker sm(s);
+    k_setup<<<1, 128, 0, s>>>(args, plan, base);
+    if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
+    k_prep<<<dim3((unsigned)std::max(1, di.sms * 2 / nprob), nprob), 256, 0, s>>>(plan);
+    if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
+    sm.mark("prep");
+    if (coop((const void*)k_sort, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+    sm.mark("sort");
+    // dominance: one launch per objective count present
+    long long item = 0;
+    for (int p = 0; p < nprob;) {
+        int q = p;
+        long long hi = item;
+        while (q < nprob && ins[q].m == ins[p].m) hi += dom_items_of(ins[q++].n2);
+        if (launch_dominance_tri_range(ins[p].m, plan, di.sms, s, item, hi, &plan->dom_ctr[ins[p].m]) !=
+            cudaSuccess)
+            return EMO_ERR_CUDA;
+        item = hi;
+        p = q;
+    }
+    sm.mark("dominance");
+    const size_t peel_smem = (size_t)(max_ncb + 1) * sizeof(int);
+    if (peel_smem > 48 * 1024) return EMO_ERR_INVALID_ARG;
+    if (coop((const void*)k_peel, di.G, peel_smem, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+    sm.mark("peel");
+    if (any_select) {
+        if (coop((const void*)k_stats, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("stats");
+        std::vector<int> m_of(nprob);
+        for (int p = 0; p < nprob; ++p) m_of[p] = ins[p].m;
+        if (launch_assoc(plan, nprob, m_of.data(), di.sms, s) != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("assoc");
+        k_rescan<<<di.sms * 2, 256, 0, s>>>(plan);
+        if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("rescan");
+        if (coop((const void*)k_csr, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("csr");
+        k_niche<<<nprob, 1024, 0, s>>>(plan);
+        if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("niche");
+    }
+    if (coop((const void*)k_finish, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+    sm.mark("finish");
+    return EMO_OK;
+}
+
+int64_t problem_bytes(const ProbIn& in)
+{
+    DevInfo di = dev_info();
+    if (!di.ok) return -1;
+    return layout_problem(in, di.G, nullptr, nullptr);
+}
+
+emo_status check_select_args(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r, int64_t n_keep,
+                             int32_t* survivors)
+{
+    if (!F || !R || !survivors) return EMO_ERR_INVALID_ARG;
+    if (!sizes_ok(n2, m) || n_r < 1 || n_keep < 1 || n_keep > n2) return EMO_ERR_INVALID_ARG;
+    if (!aligned(F, 4) || !aligned(R, 4) || !aligned(survivors, 4)) return EMO_ERR_INVALID_ARG;
+    return EMO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r)
+{
+    if (!sizes_ok(n2, m)) return 0;
+    if (op == EMO_OP_DOMINANCE) return 0;
+    int mode = op == EMO_OP_ND_RANK ? MODE_RANK : op == EMO_OP_NSGA3_SELECT ? MODE_SELECT : 0;
+    if (!mode) return 0;
+    if (mode == MODE_SELECT && n_r < 1) return 0;
+    ProbIn in = make_in(nullptr, nullptr, n2, m, mode == MODE_SELECT ? n_r : 1, n2, 0, 0, nullptr, nullptr, mode);
+    int64_t b = problem_bytes(in);
+    return b < 0 ? 0 : (size_t)(kPlanBytes + b);
+}
+
+emo_status emo_dominance(const float* F, int64_t n2, int32_t m, uint32_t* D, int64_t ld_words, int32_t* dom_count,
+                         emo_stream_t stream)
+{
+    if (!F || !D || !sizes_ok(n2, m) || ld_words < cdiv(n2, 32)) return EMO_ERR_INVALID_ARG;
+    if (!aligned(F, 4) || !aligned(D, 4) || (dom_count && !aligned(dom_count, 4))) return EMO_ERR_INVALID_ARG;
+    DevInfo di = dev_info();
+    if (!di.ok) return EMO_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dom_count && cudaMemsetAsync(dom_count, 0, (size_t)n2 * 4, s) != cudaSuccess) return EMO_ERR_CUDA;
+    const int64_t wfull = cdiv(n2, kColBlock) * 32;
+    if (ld_words > wfull &&
+        cudaMemset2DAsync(D + wfull, (size_t)ld_words * 4, 0, (size_t)(ld_words - wfull) * 4, (size_t)n2, s) !=
+            cudaSuccess)
+        return EMO_ERR_CUDA;
+    if (launch_dominance_full_c(F, n2, m, D, ld_words, dom_count, di.sms, s) != cudaSuccess) return EMO_ERR_CUDA;
+    return EMO_OK;
+}
+
+emo_status emo_nd_rank(const float* F, int64_t n2, int32_t m, int64_t n_keep, int32_t* rank, int32_t* last_rank,
+                       void* ws, size_t ws_bytes, emo_stream_t stream)
+{
+    if (!F || !rank || !sizes_ok(n2, m) || n_keep < 0 || n_keep > n2) return EMO_ERR_INVALID_ARG;
+    if (!aligned(F, 4) || !aligned(rank, 4) || (last_rank && !aligned(last_rank, 4))) return EMO_ERR_INVALID_ARG;
+    std::vector<ProbIn> ins(1, make_in(F, nullptr, n2, m, 1, n_keep, 0, 0, nullptr, nullptr, MODE_RANK));
+    ins[0].rank_out = rank;
+    ins[0].last_rank_out = last_rank;
+    return run(ins, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+emo_status emo_nsga3_select_debug(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
+                                  int64_t n_keep, uint64_t seed, uint64_t generation, int32_t* survivors,
+                                  emo_select_info* info, const emo_select_debug* dbg, void* ws, size_t ws_bytes,
+                                  emo_stream_t stream)
+{
+    emo_status st = check_select_args(F, n2, m, R, n_r, n_keep, survivors);
+    if (st != EMO_OK) return st;
+    std::vector<ProbIn> ins(1, make_in(F, R, n2, m, n_r, n_keep, seed, generation, survivors, info, MODE_SELECT));
+    if (dbg) ins[0].dbg = *dbg;
+    return run(ins, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+emo_status emo_nsga3_select(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r, int64_t n_keep,
+                            uint64_t seed, uint64_t generation, int32_t* survivors, emo_select_info* info, void* ws,
+                            size_t ws_bytes, emo_stream_t stream)
+{
+    return emo_nsga3_select_debug(F, n2, m, R, n_r, n_keep, seed, generation, survivors, info, nullptr, ws,
+                                  ws_bytes, stream);
+}
+
+static bool batch_order(const emo_problem* descs, int32_t batch, std::vector<ProbIn>& ins)
+{
+    if (!descs || batch < 1 || batch > kMaxBatch) return false;
+    ins.clear();
+    for (int b = 0; b < batch; ++b) {
+        const emo_problem& p = descs[b];
+        if (check_select_args(p.F, p.n2, p.m, p.R, p.n_r, p.n_keep, p.survivors) != EMO_OK) return false;
+        ins.push_back(make_in(p.F, p.R, p.n2, p.m, p.n_r, p.n_keep, p.seed, p.generation, p.survivors, p.info,
+                              MODE_SELECT));
+    }
+    std::stable_sort(ins.begin(), ins.end(), [](const ProbIn& a, const ProbIn& b) {
+        return a.m != b.m ? a.m < b.m : a.n2 > b.n2;
+    });
+    return true;
+}
+
+size_t emo_batch_workspace_size(const emo_problem* descs, int32_t batch)
+{
+    std::vector<ProbIn> ins;
+    if (!batch_order(descs, batch, ins)) return 0;
+    int64_t total = kPlanBytes;
+    for (auto& in : ins) {
+        int64_t b = problem_bytes(in);
+        if (b < 0) return 0;
+        total += b;
+    }
+    return (size_t)total;
+}
+
+emo_status emo_nsga3_select_batch(const emo_problem* descs, int32_t batch, void* ws, size_t ws_bytes,
+                                  emo_stream_t stream)
+{
+    std::vector<ProbIn> ins;
+    if (!batch_order(descs, batch, ins)) return EMO_ERR_INVALID_ARG;
+    return run(ins, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+emo_status emo_workspace_status(const void* ws, emo_stream_t stream, int32_t* status_out)
+{
+    if (!ws || !status_out) return EMO_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return EMO_ERR_CUDA;
+    int32_t st = 0;
+    if (cudaMemcpy(&st, &((const Plan*)ws)->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return EMO_ERR_CUDA;
+    *status_out = st;
+    return EMO_OK;
+}
+
+void emo_set_spin_budget(int64_t cycles) { g_spin_budget.store(cycles > 0 ? cycles : 0); }
+
+const char* emo_status_string(int status)
+{
+    switch (status) {
+    case EMO_OK: return "ok";
+    case EMO_ERR_INVALID_ARG: return "invalid argument";
+    case EMO_ERR_NONFINITE: return "non-finite objective or zero/non-finite reference direction";
+    case EMO_ERR_WORKSPACE: return "workspace too small";
+    case EMO_ERR_CUDA: return "CUDA runtime error";
+    case EMO_ERR_TIMEOUT: return "bounded device wait ran out";
+    case EMO_ERR_NOT_IMPLEMENTED: return "not implemented";
+    default: return "unknown status";
+    }
+}
+
+int32_t emo_version(void) { return 100; }
+
+void emo_set_stage_timing(int32_t enable) { g_timing.store(enable ? 1 : 0); }
+
+int32_t emo_stage_times(float* ms_out, const char** names_out, int32_t max_n)
+{
+    if (!g_st.created || g_st.n == 0) return 0;
+    if (cudaEventSynchronize(g_st.ev[g_st.n]) != cudaSuccess) return -1;
+    int n = std::min(g_st.n, (int)max_n);
+    for (int i = 0; i < n; ++i) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, g_st.ev[i], g_st.ev[i + 1]) != cudaSuccess) return -1;
+        if (ms_out) ms_out[i] = ms;
+        if (names_out) names_out[i] = g_st.name[i];
+    }
+    return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,198 @@
+// Set-up, input validation and the lexicographic ordering of the points.
+//
+// The points are put in lexicographic order of (f_1, ..., f_m) by a stable
+// LSD radix sort (8-bit digits of an order-preserving uint32 key, objective
+// m first, objective 1 last). In that order a point can only be dominated by
+// points before it (Section IV-A: p dominates q implies f(p) <= f(q)
+// componentwise, hence f(p) <=_lex f(q)), which is what lets the dominance
+// kernel compute and store only the upper triangle of D. Runs of identical
+// objective vectors (which never dominate each other) are recorded so the
+// dominance kernel can clear them.
+#include "emo_kernels.cuh"
+#include "group_radix.cuh"
+
+namespace emo {
+
+// One thread per problem: carve the workspace, zero the scalars; thread 0
+// then splits the cooperative grid into CTA groups and counts work items.
+__global__ void k_setup(SetupArgs a, Plan* plan, char* ws)
+{
+    const int t = threadIdx.x;
+    if (t < a.nprob) {
+        ProbDev d;
+        layout_problem(a.in[t], a.G, ws + a.in[t].ws_off, &d);
+        plan->p[t] = d;
+        char* sc = (char*)d.sc;
+        for (size_t i = 0; i < sizeof(Scal); ++i) sc[i] = 0;
+    }
+    __syncthreads();
+    if (t == 0) {
+        plan->nprob = a.nprob;
+        plan->G = a.G;
+        plan->spin_budget = a.spin_budget;
+        for (int i = 0; i <= kMaxM; ++i) plan->dom_ctr[i] = 0;
+        plan->asc_next = 0;
+        plan->status = 0;
+        // CTA groups proportional to n2^2 (the dominance and peeling work),
+        // at least one CTA each.
+        double tot = 0.0;
+        for (int p = 0; p < a.nprob; ++p) tot += (double)a.in[p].n2 * (double)a.in[p].n2;
+        int extra = a.G - a.nprob, given = 0;
+        int cnt[kMaxBatch];
+        for (int p = 0; p < a.nprob; ++p) {
+            double w = (double)a.in[p].n2 * (double)a.in[p].n2 / tot;
+            cnt[p] = 1 + (int)(w * extra);
+            given += cnt[p];
+        }
+        for (int p = 0; given < a.G; p = (p + 1) % a.nprob) { cnt[p]++; given++; }
+        int acc = 0;
+        for (int p = 0; p < a.nprob; ++p) { plan->grp_first[p] = acc; acc += cnt[p]; }
+        plan->grp_first[a.nprob] = acc;
+        long long di = 0, ai = 0;
+        for (int p = 0; p < a.nprob; ++p) {
+            plan->dom_item_start[p] = di;
+            di += dom_items_of(a.in[p].n2);
+            plan->asc_item_start[p] = ai;
+            if (a.in[p].mode == MODE_SELECT) ai += cdiv(a.in[p].n2, kAscPointsPerItem);
+        }
+        plan->dom_item_start[a.nprob] = di;
+        plan->dom_items = di;
+        plan->asc_item_start[a.nprob] = ai;
+    }
+}
+
+// Validation and initialisation, grid (x, problem).
+__global__ void k_prep(Plan* plan)
+{
+    const ProbDev& d = plan->p[blockIdx.y];
+    const ProbIn& in = d.in;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n2 = in.n2, m = in.m;
+    bool bad = false;
+    for (int64_t i = tid; i < n2 * m; i += stride)
+        if (!isfinite(in.F[i])) bad = true;
+    for (int64_t s = tid; s < d.n2p; s += stride) {
+        d.idx[s] = (int32_t)s;
+        d.cnt[s] = 0;
+        d.rank_s[s] = kNotRanked;
+        d.flag[s] = 0;
+    }
+    for (int64_t i = tid; i < n2; i += stride) d.rank_o[i] = kNotRanked;
+    for (int64_t c = tid; c < 2 * (int64_t)d.ncb; c += stride) d.front_n[c] = 0;
+    for (int64_t c = tid; c < d.ncb; c += stride) d.minrs[c] = INT32_MAX;
+    if (in.mode == MODE_SELECT) {
+        for (int64_t j = tid; j < in.n_r; j += stride) {
+            double rr = 0.0;
+            bool fin = true;
+            for (int k = 0; k < m; ++k) {
+                float r = in.R[j * m + k];
+                fin = fin && isfinite(r);
+                rr += (double)r * (double)r;
+            }
+            if (!fin || !(rr > 0.0)) bad = true;
+            double inv = fin && rr > 0.0 ? 1.0 / sqrt(rr) : 0.0;
+            for (int k = 0; k < m; ++k) d.rhat[j * m + k] = (float)((double)in.R[j * m + k] * inv);
+            d.rho[j] = 0;
+            d.lcnt[j] = 0;
+        }
+    }
+    if (bad) set_status(d.sc, EMO_ERR_NONFINITE);
+}
+
+// Lexicographic order, sorted objective keys and runs of equal points.
+__global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
+{
+    const Group g = group_of(plan);
+    const ProbDev& d = plan->p[g.prob];
+    const ProbIn& in = d.in;
+    const long long budget = plan->spin_budget;
+    if (ld_volatile(&d.sc->status) != 0) return;
+    const int64_t n2 = in.n2;
+    const int m = in.m;
+    const int gs = (int)max((int64_t)1, min((int64_t)g.size, cdiv(n2, 4096)));
+    const float* F = in.F;
+
+    int buf = 0;
+    for (int k = m - 1; k >= 0; --k) {
+        for (int shift = 0; shift < 32; shift += kRadixBits) {
+            const int32_t* src = d.idx + (int64_t)buf * d.n2p;
+            int32_t* dst = d.idx + (int64_t)(buf ^ 1) * d.n2p;
+            bool skipped = false;
+            auto key = [&](int32_t v) { return float_key(__ldg(&F[(int64_t)v * m + k])); };
+            if (!radix_pass(d, g, gs, budget, n2, src, dst, shift, key, skipped)) return;
+            if (!skipped) buf ^= 1;
+        }
+    }
+    if (g.rank == 0 && threadIdx.x == 0) d.sc->idx_buf = buf;
+    const int32_t* idx = d.idx + (int64_t)buf * d.n2p;
+
+    // objective keys 2..m in sorted order (padding = -inf), run starts
+    const int64_t chunk = cdiv(d.n2p, g.size);
+    const int64_t lo = min(d.n2p, chunk * g.rank), hi = min(d.n2p, lo + chunk);
+    const int mk = m - 1;
+    for (int64_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
+        if (s < n2) {
+            const int64_t v = __ldcg(&idx[s]);
+            for (int k = 1; k < m; ++k) d.keys[s * mk + k - 1] = F[v * m + k] + 0.0f;
+        } else {
+            for (int k = 1; k < m; ++k) d.keys[s * mk + k - 1] = -INFINITY;
+        }
+    }
+    auto is_start = [&](int64_t s) -> bool {
+        if (s == 0 || s >= n2) return true;
+        const int64_t a = __ldcg(&idx[s]), b = __ldcg(&idx[s - 1]);
+        for (int k = 0; k < m; ++k)
+            if (F[a * m + k] != F[b * m + k]) return true;
+        return false;
+    };
+    // inclusive max-scan of (start ? s : 0) across the group
+    __shared__ int s_warp[33];
+    int local = -1;
+    for (int64_t s = lo + threadIdx.x; s < hi; s += blockDim.x)
+        if (is_start(s)) local = max(local, (int)s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local = max(local, __shfl_xor_sync(0xffffffffu, local, o));
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int mx = -1;
+        for (int w = 0; w < kCoopThreads / 32; ++w) mx = max(mx, s_warp[w]);
+        d.hist[g.rank] = mx;
+    }
+    if (!group_sync(d.sc, g.size, budget)) return;
+    __shared__ int s_carry;
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int r = 0; r < g.rank; ++r) c = max(c, __ldcg(&d.hist[r]));
+        s_carry = c;
+    }
+    __syncthreads();
+    int carry = s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = lo; base < hi; base += blockDim.x) {
+        const int64_t s = base + threadIdx.x;
+        int v = (s < hi && is_start(s)) ? (int)s : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v = max(v, y);
+        }
+        if (lane == 31) s_warp[warp] = v;
+        __syncthreads();
+        int pre = carry;
+        for (int w = 0; w < warp; ++w) pre = max(pre, s_warp[w]);
+        int rs = max(pre, v);
+        if (s < hi) {
+            d.runstart[s] = rs;
+            if (rs < s) atomicMin(&d.minrs[s / kColBlock], rs);
+        }
+        __syncthreads();
+        int tmax = carry;
+        for (int w = 0; w < kCoopThreads / 32; ++w) tmax = max(tmax, s_warp[w]);
+        carry = tmax;
+        __syncthreads();
+    }
+}
+
+}  // namespace emo

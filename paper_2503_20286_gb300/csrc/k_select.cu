@@ -1,0 +1,431 @@
+// Normalisation, association, niche counts, niching and survivor extraction
+// (Algorithm S.1 with Algorithm S.5; Section IV-A "Normalization",
+// "Association", "Niche Count Calculation", "Niche Selection").
+//
+// Precision: everything that decides an index is taken in the same FP64
+// arithmetic, operation order and rounding as the FP64 reference statement
+// of the method (no fused multiply-add: explicit __d*_rn intrinsics):
+//   * ideal point z = min over S (exact in float);
+//   * ASF extreme points: an FP32 pass bounds the minimum, points within the
+//     FP32 error band are re-evaluated in FP64;
+//   * hyperplane intercepts: Gaussian elimination with partial pivoting in
+//     FP64 on one thread (m <= 16), nadir fallback;
+//   * association: an FP32 scan over all references keeps the three largest
+//     projections f.r/|r|; references whose projection lies within a
+//     rigorous error band of the best are re-evaluated with the FP64
+//     perpendicular distance d^2 = sum (f_k - t r_k)^2, t = f.r / r.r.
+#include "emo_kernels.cuh"
+
+namespace emo {
+
+// ------------------------------------------------------------ FP64 helpers
+__device__ __forceinline__ double fnorm64(float F, float z, double a)
+{
+    return __ddiv_rn(__dsub_rn((double)F, (double)z), a);
+}
+
+// Perpendicular distance^2 of normalised point fn[0..m) to the line of r.
+__device__ inline double perp_d2(const double* fn, const float* r, int m)
+{
+    double rr = 0.0, fr = 0.0;
+    for (int k = 0; k < m; ++k) rr = __dadd_rn(rr, __dmul_rn((double)r[k], (double)r[k]));
+    for (int k = 0; k < m; ++k) fr = __dadd_rn(fr, __dmul_rn(fn[k], (double)r[k]));
+    const double t = __ddiv_rn(fr, rr);
+    double d2 = 0.0;
+    for (int k = 0; k < m; ++k) {
+        const double e = __dsub_rn(fn[k], __dmul_rn(t, (double)r[k]));
+        d2 = __dadd_rn(d2, __dmul_rn(e, e));
+    }
+    return d2;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// ------------------------------------------------------------ k_stats
+// Ideal point, ASF extreme points, nadir point, intercepts (Algorithm S.5).
+__global__ void __launch_bounds__(kCoopThreads, 1) k_stats(Plan* plan)
+{
+    const Group g = group_of(plan);
+    const ProbDev& d = plan->p[g.prob];
+    const ProbIn& in = d.in;
+    const long long budget = plan->spin_budget;
+    if (in.mode != MODE_SELECT || ld_volatile(&d.sc->status) != 0) return;
+    Scal* sc = d.sc;
+    const int m = in.m, tid = threadIdx.x, lane = tid & 31;
+    const int nS = ld_volatile(&sc->nS);
+    const float* F = in.F;
+    const int64_t stride = (int64_t)g.size * blockDim.x;
+    const int64_t t0 = (int64_t)g.rank * blockDim.x + tid;
+    __shared__ uint32_t s_u32[kMaxM];
+    __shared__ unsigned long long s_u64[kMaxM];
+    __shared__ float s_z[kMaxM];
+
+    // 1. ideal point: keep ~key maxima (Scal is zero-initialised)
+    if (tid < kMaxM) s_u32[tid] = 0u;
+    __syncthreads();
+    {
+        uint32_t best[kMaxM];
+#pragma unroll
+        for (int k = 0; k < kMaxM; ++k) best[k] = 0u;
+        for (int64_t i = t0; i < nS; i += stride) {
+            const int64_t v = d.slist[i];
+#pragma unroll
+            for (int k = 0; k < kMaxM; ++k)
+                if (k < m) best[k] = max(best[k], ~float_key(F[v * m + k]));
+        }
+#pragma unroll
+        for (int k = 0; k < kMaxM; ++k) {
+            if (k >= m) break;
+            uint32_t b = best[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+            if (lane == 0 && b) atomicMax(&s_u32[k], b);
+        }
+    }
+    __syncthreads();
+    if (tid < m && s_u32[tid]) atomicMax(&sc->zkey[tid], s_u32[tid]);
+    if (!group_sync(sc, g.size, budget)) return;
+    if (tid < m) s_z[tid] = key_float(~__ldcg(&sc->zkey[tid]));
+    if (tid < kMaxM) { s_u32[tid] = 0u; s_u64[tid] = 0ull; }
+    __syncthreads();
+
+    // 2. FP32 ASF minima per axis (stored as ~bits maxima) and FP64 nadir
+    {
+        for (int64_t i = t0; i < nS; i += stride) {
+            const int64_t v = d.slist[i];
+            float dev[kMaxM];
+#pragma unroll
+            for (int k = 0; k < kMaxM; ++k) dev[k] = k < m ? F[v * m + k] - s_z[k] : 0.0f;
+#pragma unroll
+            for (int k = 0; k < kMaxM; ++k) {
+                if (k >= m) break;
+                const double nd = __dsub_rn((double)F[v * m + k], (double)s_z[k]);
+                atomicMax(&s_u64[k], dbits(nd));
+            }
+            for (int j = 0; j < m; ++j) {
+                float asf = 0.0f;
+#pragma unroll
+                for (int k = 0; k < kMaxM; ++k)
+                    if (k < m) asf = fmaxf(asf, k == j ? dev[k] : dev[k] * 1.0e6f);
+                atomicMax(&s_u32[j], ~__float_as_uint(asf));
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < m) {
+        atomicMax(&sc->asf32[tid], s_u32[tid]);
+        atomicMax(&sc->nadir[tid], s_u64[tid]);
+    }
+    if (!group_sync(sc, g.size, budget)) return;
+
+    // 3. exact FP64 ASF of the candidates within the FP32 error band
+    if (tid < kMaxM) s_u64[tid] = 0ull;
+    __syncthreads();
+    __shared__ float s_lim[kMaxM];
+    if (tid < m) {
+        const float mn = __uint_as_float(~__ldcg(&sc->asf32[tid]));
+        s_lim[tid] = mn * (1.0f + 0x1p-18f) + 1e-30f;
+    }
+    __syncthreads();
+    auto asf64 = [&](int64_t v, int j) {
+        double mx = -INFINITY;
+        for (int k = 0; k < m; ++k) {
+            const double w = k == j ? 1.0 : 1e-6;
+            const double t = __ddiv_rn(__dsub_rn((double)F[v * m + k], (double)s_z[k]), w);
+            if (t > mx) mx = t;
+        }
+        return mx;
+    };
+    auto asf32 = [&](int64_t v, int j) {
+        float asf = 0.0f;
+        for (int k = 0; k < m; ++k) {
+            const float dv = F[v * m + k] - s_z[k];
+            asf = fmaxf(asf, k == j ? dv : dv * 1.0e6f);
+        }
+        return asf;
+    };
+    for (int64_t i = t0; i < nS; i += stride) {
+        const int64_t v = d.slist[i];
+        for (int j = 0; j < m; ++j)
+            if (asf32(v, j) <= s_lim[j]) atomicMax(&s_u64[j], ~dbits(asf64(v, j)));
+    }
+    __syncthreads();
+    if (tid < m) atomicMax(&sc->asf64[tid], s_u64[tid]);
+    if (!group_sync(sc, g.size, budget)) return;
+
+    // 4. lowest index attaining the FP64 minimum (stored as INT32_MAX - i maxima)
+    __shared__ unsigned long long s_best[kMaxM];
+    if (tid < m) s_best[tid] = ~__ldcg(&sc->asf64[tid]);
+    __syncthreads();
+    for (int64_t i = t0; i < nS; i += stride) {
+        const int64_t v = d.slist[i];
+        for (int j = 0; j < m; ++j)
+            if (asf32(v, j) <= s_lim[j] && dbits(asf64(v, j)) == s_best[j])
+                atomicMax(&sc->ext[j], INT32_MAX - (int)v);
+    }
+    if (!group_sync(sc, g.size, budget)) return;
+
+    // 5. intercepts by Gaussian elimination with partial pivoting (FP64)
+    if (g.rank == 0 && tid == 0) {
+        double A[kMaxM][kMaxM], rhs[kMaxM], b[kMaxM], a[kMaxM];
+        int ext[kMaxM];
+        double maxabs = 0.0;
+        for (int j = 0; j < m; ++j) {
+            const int e = ld_volatile(&sc->ext[j]);
+            if (e <= 0) {  // no candidate attained the minimum (non-finite values)
+                set_status(sc, EMO_ERR_NONFINITE);
+                return;
+            }
+            ext[j] = INT32_MAX - e;
+            rhs[j] = 1.0;
+            for (int k = 0; k < m; ++k) {
+                A[j][k] = __dsub_rn((double)F[(int64_t)ext[j] * m + k], (double)s_z[k]);
+                maxabs = fmax(maxabs, fabs(A[j][k]));
+            }
+        }
+        int singular = 0;
+        for (int col = 0; col < m && !singular; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < m; ++r)
+                if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+            if (!(fabs(A[piv][col]) > __dmul_rn(1e-12, maxabs))) { singular = 1; break; }
+            if (piv != col) {
+                for (int c = 0; c < m; ++c) { double t = A[col][c]; A[col][c] = A[piv][c]; A[piv][c] = t; }
+                double t = rhs[col]; rhs[col] = rhs[piv]; rhs[piv] = t;
+            }
+            for (int r = col + 1; r < m; ++r) {
+                const double f = __ddiv_rn(A[r][col], A[col][col]);
+                for (int c = col; c < m; ++c) A[r][c] = __dsub_rn(A[r][c], __dmul_rn(f, A[col][c]));
+                rhs[r] = __dsub_rn(rhs[r], __dmul_rn(f, rhs[col]));
+            }
+        }
+        int fallback = singular;
+        if (!singular) {
+            for (int col = m - 1; col >= 0; --col) {
+                double s = rhs[col];
+                for (int c = col + 1; c < m; ++c) s = __dsub_rn(s, __dmul_rn(A[col][c], b[c]));
+                b[col] = __ddiv_rn(s, A[col][col]);
+            }
+            for (int k = 0; k < m; ++k) {
+                a[k] = __ddiv_rn(1.0, b[k]);
+                if (!isfinite(a[k]) || a[k] <= 1e-10) fallback = 1;
+            }
+        }
+        if (fallback) {
+            for (int k = 0; k < m; ++k) {
+                a[k] = __longlong_as_double((long long)__ldcg(&sc->nadir[k]));
+                if (a[k] <= 1e-10) a[k] = 1.0;
+            }
+        }
+        for (int k = 0; k < m; ++k) {
+            sc->a[k] = a[k];
+            sc->inv_a32[k] = (float)__ddiv_rn(1.0, a[k]);
+            sc->z[k] = s_z[k];
+            sc->ext[k] = ext[k];
+        }
+        sc->fallback = fallback;
+        __threadfence();
+    }
+}
+
+// ------------------------------------------------------------ association
+// Error band of the FP32 projection scan, relative to |f|: covers the
+// rounding of f - z, 1/a, the product, the unit reference and the dot
+// product (<= (m + 8) u |f| each way), plus the FP64 rounding gap.
+__device__ __forceinline__ float assoc_band(float fnorm, int m) { return fnorm * (float)(2 * m + 40) * 0x1p-24f; }
+
+template <int M>
+__device__ __forceinline__ void load_point32(const ProbDev& d, const Scal* sc, int64_t v, float* f, float& nrm)
+{
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        f[k] = (d.in.F[v * M + k] - sc->z[k]) * sc->inv_a32[k];
+        s = fmaf(f[k], f[k], s);
+    }
+    nrm = sqrtf(s) * 1.0001f;
+}
+
+// Exact decision between candidate references (FP64, reference formula).
+__device__ inline void decide64(const ProbDev& d, const Scal* sc, int64_t v, int m, const int* cand, int nc,
+                                int& best_j, double& best_d2)
+{
+    double fn[kMaxM];
+    for (int k = 0; k < m; ++k) fn[k] = fnorm64(d.in.F[v * m + k], sc->z[k], sc->a[k]);
+    best_j = -1;
+    best_d2 = INFINITY;
+    for (int c = 0; c < nc; ++c) {
+        const int j = cand[c];
+        const double d2 = perp_d2(fn, d.in.R + (int64_t)j * m, m);
+        if (d2 < best_d2 || (d2 == best_d2 && j < best_j)) { best_d2 = d2; best_j = j; }
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) k_assoc_m(Plan* plan, int pfirst, int plast)
+{
+    constexpr int P = 2;             // points per thread
+    constexpr int TR = 1024;         // references per shared-memory tile
+    __shared__ float s_r[TR * M];
+    const int tid = threadIdx.x;
+    for (int p = pfirst; p < plast; ++p) {
+        const ProbDev& d = plan->p[p];
+        const Scal* sc = d.sc;
+        if (d.in.mode != MODE_SELECT || d.in.m != M || ld_volatile(&sc->status) != 0) continue;
+        const int nS = ld_volatile(&sc->nS);
+        const int nr = d.in.n_r;
+        const int per_block = 256 * P;
+        for (int64_t base = (int64_t)blockIdx.x * per_block; base < nS; base += (int64_t)gridDim.x * per_block) {
+            float f[P][M], nrm[P], b1[P], b2[P], b3[P];
+            int i1[P], i2[P];
+            int64_t v[P];
+            bool live[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int64_t s = base + q * 256 + tid;
+                live[q] = s < nS;
+                v[q] = live[q] ? d.slist[s] : 0;
+                if (live[q]) load_point32<M>(d, sc, v[q], f[q], nrm[q]);
+                else {
+#pragma unroll
+                    for (int k = 0; k < M; ++k) f[q][k] = 0.0f;
+                    nrm[q] = 0.0f;
+                }
+                b1[q] = b2[q] = b3[q] = -INFINITY;
+                i1[q] = i2[q] = -1;
+            }
+            for (int t0 = 0; t0 < nr; t0 += TR) {
+                const int nt = min(TR, nr - t0);
+                __syncthreads();
+                for (int i = tid; i < nt * M; i += 256) s_r[i] = d.rhat[(int64_t)t0 * M + i];
+                __syncthreads();
+                for (int jj = 0; jj < nt; ++jj) {
+                    float r[M];
+#pragma unroll
+                    for (int k = 0; k < M; ++k) r[k] = s_r[jj * M + k];
+                    const int j = t0 + jj;
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        float gq = f[q][0] * r[0];
+#pragma unroll
+                        for (int k = 1; k < M; ++k) gq = fmaf(f[q][k], r[k], gq);
+                        if (gq > b3[q]) {
+                            if (gq > b2[q]) {
+                                b3[q] = b2[q];
+                                if (gq > b1[q]) { b2[q] = b1[q]; i2[q] = i1[q]; b1[q] = gq; i1[q] = j; }
+                                else { b2[q] = gq; i2[q] = j; }
+                            } else {
+                                b3[q] = gq;
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                if (!live[q]) continue;
+                const float band = assoc_band(nrm[q], M);
+                const float lim = b1[q] - band;
+                int cand[2];
+                int nc = 0;
+                if ((b3[q] >= lim && nr > 2) || i1[q] < 0 || !isfinite(lim)) {
+                    const int slot = atomicAdd(&d.sc->nflag, 1);
+                    d.flagged[slot] = (int32_t)v[q];
+                    continue;
+                }
+                cand[nc++] = i1[q];
+                if (i2[q] >= 0 && b2[q] >= lim) cand[nc++] = i2[q];
+                int bj;
+                double bd2;
+                decide64(d, sc, v[q], M, cand, nc, bj, bd2);
+                d.pi[v[q]] = bj;
+                d.d64[v[q]] = __dsqrt_rn(bd2);
+            }
+        }
+    }
+}
+
+// All-reference scan for points whose FP32 band holds three or more
+// references: one warp per point, exact FP64 over every candidate.
+__global__ void __launch_bounds__(256) k_rescan(Plan* plan)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int p = 0; p < plan->nprob; ++p) {
+        const ProbDev& d = plan->p[p];
+        Scal* sc = d.sc;
+        if (d.in.mode != MODE_SELECT || ld_volatile(&sc->status) != 0) continue;
+        const int nflag = ld_volatile(&sc->nflag);
+        const int m = d.in.m, nr = d.in.n_r;
+        for (int64_t w = gw; w < nflag; w += nw) {
+            const int64_t v = d.flagged[w];
+            float f[kMaxM];
+            float s = 0.0f;
+            for (int k = 0; k < m; ++k) {
+                f[k] = (d.in.F[v * m + k] - sc->z[k]) * sc->inv_a32[k];
+                s = fmaf(f[k], f[k], s);
+            }
+            const float band = assoc_band(sqrtf(s) * 1.0001f, m);
+            auto proj = [&](int j) {
+                const float* r = d.rhat + (int64_t)j * m;
+                float gq = f[0] * r[0];
+                for (int k = 1; k < m; ++k) gq = fmaf(f[k], r[k], gq);
+                return gq;
+            };
+            float gmax = -INFINITY;
+            for (int j = lane; j < nr; j += 32) gmax = fmaxf(gmax, proj(j));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+            const float lim = gmax - band;
+            double fn[kMaxM];
+            for (int k = 0; k < m; ++k) fn[k] = fnorm64(d.in.F[v * m + k], sc->z[k], sc->a[k]);
+            double bd2 = INFINITY;
+            int bj = INT32_MAX;
+            const bool all_refs = !isfinite(lim);  // overflowed projections: decide every reference in FP64
+            for (int j = lane; j < nr; j += 32) {
+                if (all_refs || proj(j) >= lim) {
+                    const double d2 = perp_d2(fn, d.in.R + (int64_t)j * m, m);
+                    if (d2 < bd2 || (d2 == bd2 && j < bj)) { bd2 = d2; bj = j; }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double od = __shfl_xor_sync(0xffffffffu, bd2, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                if (od < bd2 || (od == bd2 && oj < bj)) { bd2 = od; bj = oj; }
+            }
+            if (lane == 0) {
+                if (bj == INT32_MAX) {  // every distance was NaN
+                    set_status(d.sc, EMO_ERR_NONFINITE);
+                    bj = 0;
+                }
+                d.pi[v] = bj;
+                d.d64[v] = __dsqrt_rn(bd2);
+            }
+        }
+    }
+}
+
+// Host launcher: one instantiation per objective count.
+cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, cudaStream_t s)
+{
+    for (int p = 0; p < nprob;) {
+        int q = p;
+        while (q < nprob && m_of[q] == m_of[p]) ++q;
+        const unsigned grid = (unsigned)sms * 4;
+        switch (m_of[p]) {
+#define X(MM) \
+    case MM: k_assoc_m<MM><<<grid, 256, 0, s>>>(plan, p, q); break;
+            X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+#undef X
+        default: return cudaErrorInvalidValue;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        p = q;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace emo

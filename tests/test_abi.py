@@ -1,0 +1,71 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every entry
+point declared in include/emo.h; host-side argument checks reject bad calls
+before anything is launched. No compute call runs here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "emo.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(emo_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2503_20286_gb300 import build, _binding
+    build.build()
+    return _binding.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("emo_dominance", "emo_nd_rank", "emo_nsga3_select", "emo_nsga3_select_batch",
+                 "emo_workspace_size", "emo_batch_workspace_size"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2503_20286_gb300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(emo_[a-z0-9_]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_status_strings_and_version(lib):
+    from paper_2503_20286_gb300 import _binding as b
+    assert b.emo_version() >= 100
+    for code in range(7):
+        assert b.emo_status_string(code)
+    assert b.emo_status_string(99) == "unknown status"
+
+
+def test_host_argument_checks_reject_before_launch(lib):
+    L = lib
+    # null pointers / bad sizes are refused on the host (no CUDA call)
+    assert L.emo_dominance(None, 10, 3, None, 1, None, None) == 1
+    assert L.emo_dominance(ctypes.c_void_p(256), 10, 1, ctypes.c_void_p(256), 1, None, None) == 1
+    assert L.emo_dominance(ctypes.c_void_p(256), 100, 3, ctypes.c_void_p(256), 3, None, None) == 1  # ld < 4
+    assert L.emo_nsga3_select(None, 10, 3, None, 5, 5, 0, 0, None, None, None, 0, None) == 1
+    p = ctypes.c_void_p(256)
+    assert L.emo_nsga3_select(p, 10, 3, p, 5, 11, 0, 0, p, None, p, 1 << 20, None) == 1  # n_keep > n2
+    assert L.emo_nsga3_select(p, 10, 17, p, 5, 5, 0, 0, p, None, p, 1 << 20, None) == 1  # m > 16
+    assert L.emo_nsga3_select(p, 10, 3, p, 0, 5, 0, 0, p, None, p, 1 << 20, None) == 1   # no references
+    assert L.emo_nd_rank(p, 0, 3, 0, p, None, p, 1 << 20, None) == 1                      # n2 = 0
+    assert L.emo_nd_rank(p, 10, 3, 11, p, None, p, 1 << 20, None) == 1                    # n_keep > n2
+    assert L.emo_nsga3_select_batch(None, 1, p, 1 << 20, None) == 1
+    assert L.emo_workspace_size(2, 0, 3, 5) == 0
+    assert L.emo_workspace_size(2, 10, 1, 5) == 0
+    assert L.emo_workspace_size(7, 10, 3, 5) == 0
+    assert L.emo_workspace_size(0, 10, 3, 5) == 0    # dominance needs no workspace
+    assert L.emo_workspace_status(None, None, None) == 1
