@@ -128,7 +128,9 @@ emo_status emo_nd_rank(const float* F, int64_t n2, int32_t m, int64_t n_keep, in
  * the ideal point, ASF extreme points and hyperplane intercepts with the
  * nadir fallback (Algorithm S.5; FP64), association to the reference lines
  * by perpendicular distance, niche counts, and niching of the last front.
- *   R          [n_r*m] reference directions, finite, non-zero rows.
+ *   R          [n_r*m] reference directions: finite, non-negative, non-zero
+ *              rows (Das-Dennis points of the unit simplex are). A negative
+ *              component gives EMO_ERR_INVALID_ARG on the device.
  *   n_keep     N, 1 <= N <= n2.
  *   seed, generation  key and counter of the Philox-4x32-10 stream that
  *              breaks niching ties (same inputs give the same survivors).

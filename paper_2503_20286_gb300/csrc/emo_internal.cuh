@@ -76,6 +76,7 @@ struct Scal {
     int32_t front_total[2];  // members of the current / next front
     int32_t idx_buf;         // idx half holding the sorted order
     int32_t lbuf;            // llist half holding the sorted candidate lists
+    int32_t rbuf;            // rord half holding the angle order
     uint32_t zkey[kMaxM];
     uint32_t asf32[kMaxM];
     unsigned long long asf64[kMaxM];
@@ -110,7 +111,11 @@ struct ProbDev {
     int32_t* pi;             // [n2] associated reference
     double* d64;             // [n2] perpendicular distance (FP64)
     float* rhat;             // [n_r][m] unit reference directions (FP32)
-    int32_t* flagged;        // [n2] points for the all-reference scan
+    int32_t* rord;           // [2][n_r] references sorted by polar angle from axis 1 (ping-pong)
+    float* rphi;             // [n_r] sorted polar angles
+    float* rsort;            // [n_r][m] unit directions in polar-angle order
+    int32_t* flagged;        // [n2] points for the exhaustive FP64 scan
+    float* flagged_bound;    // [n2] angular half-width of that scan (inf = all references)
     int32_t* rho;            // [n_r] niche counts of P (evolving during niching)
     int32_t* lcnt;           // [n_r] last-front members per reference (evolving)
     int32_t* loff;           // [n_r + 1] CSR offsets of the candidate lists
@@ -183,7 +188,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
     int64_t o_hist = take(int64_t(G) * kRadix * 4);
     int64_t o_flag = take((n2p + 1) * 4);
     int64_t o_pi = 0, o_d64 = 0, o_rhat = 0, o_flagged = 0, o_rho = 0, o_lcnt = 0, o_loff = 0,
-            o_llist = 0, o_fen = 0, o_ekeys = 0, o_elist = 0;
+            o_llist = 0, o_fen = 0, o_ekeys = 0, o_elist = 0, o_rord = 0, o_rphi = 0, o_rsort = 0, o_fbound = 0;
     if (in.mode == MODE_SELECT) {
         o_pi = take(n2 * 4);
         o_d64 = take(n2 * 8);
@@ -196,6 +201,10 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         o_fen = take(n2 * 4);
         o_ekeys = take(nr * 8);
         o_elist = take(nr * 4);
+        o_rord = take(2 * nr * 4);
+        o_rphi = take(nr * 4);
+        o_rsort = take(nr * m * 4);
+        o_fbound = take(n2 * 4);
     }
     int64_t o_D = take(ntiles * 4096);
     if (base && d) {
@@ -228,6 +237,10 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         d->fen = in.mode == MODE_SELECT ? (int32_t*)(base + o_fen) : nullptr;
         d->ekeys = in.mode == MODE_SELECT ? (unsigned long long*)(base + o_ekeys) : nullptr;
         d->elist = in.mode == MODE_SELECT ? (int32_t*)(base + o_elist) : nullptr;
+        d->rord = in.mode == MODE_SELECT ? (int32_t*)(base + o_rord) : nullptr;
+        d->rphi = in.mode == MODE_SELECT ? (float*)(base + o_rphi) : nullptr;
+        d->rsort = in.mode == MODE_SELECT ? (float*)(base + o_rsort) : nullptr;
+        d->flagged_bound = in.mode == MODE_SELECT ? (float*)(base + o_fbound) : nullptr;
         d->D = (uint32_t*)(base + o_D);
     }
     return off;
@@ -368,6 +381,15 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     }
     return c;
 }
+// Polar angle of a direction from objective axis 1, atan2(|v_2..m|, v_1):
+// well conditioned everywhere (unlike acos of a cosine near 0).
+__device__ __forceinline__ float polar_angle(const float* v, int m)
+{
+    float s = 0.0f;
+    for (int k = 1; k < m; ++k) s = fmaf(v[k], v[k], s);
+    return atan2f(sqrtf(s), v[0]);
+}
+
 // Niching stream: key = seed, counter = (j, 2 c + tag, generation).
 __device__ __forceinline__ uint32_t niche_random(uint64_t seed, uint64_t gen, uint32_t j, uint32_t c, uint32_t tag)
 {

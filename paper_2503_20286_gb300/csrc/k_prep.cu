@@ -84,17 +84,20 @@ __global__ void k_prep(Plan* plan)
     if (in.mode == MODE_SELECT) {
         for (int64_t j = tid; j < in.n_r; j += stride) {
             double rr = 0.0;
-            bool fin = true;
+            bool fin = true, neg = false;
             for (int k = 0; k < m; ++k) {
                 float r = in.R[j * m + k];
                 fin = fin && isfinite(r);
+                neg = neg || r < 0.0f;
                 rr += (double)r * (double)r;
             }
             if (!fin || !(rr > 0.0)) bad = true;
+            if (neg) set_status(d.sc, EMO_ERR_INVALID_ARG);  // directions lie in the non-negative orthant
             double inv = fin && rr > 0.0 ? 1.0 / sqrt(rr) : 0.0;
             for (int k = 0; k < m; ++k) d.rhat[j * m + k] = (float)((double)in.R[j * m + k] * inv);
             d.rho[j] = 0;
             d.lcnt[j] = 0;
+            d.rord[j] = (int32_t)j;
         }
     }
     if (bad) set_status(d.sc, EMO_ERR_NONFINITE);
@@ -192,6 +195,29 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
         for (int w = 0; w < kCoopThreads / 32; ++w) tmax = max(tmax, s_warp[w]);
         carry = tmax;
         __syncthreads();
+    }
+
+    // reference directions in order of their polar angle from axis 1 (the
+    // index of the association scan)
+    if (in.mode != MODE_SELECT) return;
+    const int nr = in.n_r;
+    const int gr = (int)max((int64_t)1, min((int64_t)g.size, cdiv(nr, 4096)));
+    const float* rhat = d.rhat;
+    auto rkey = [&](int32_t j) { return float_key(polar_angle(rhat + (int64_t)j * m, m)); };
+    int rb = 0;
+    for (int shift = 0; shift < 32; shift += kRadixBits) {
+        bool skipped = false;
+        if (!radix_pass(d, g, gr, budget, nr, d.rord + (int64_t)rb * nr, d.rord + (int64_t)(rb ^ 1) * nr, shift, rkey,
+                        skipped))
+            return;
+        if (!skipped) rb ^= 1;
+    }
+    if (g.rank == 0 && threadIdx.x == 0) d.sc->rbuf = rb;
+    const int32_t* ro = d.rord + (int64_t)rb * nr;
+    for (int64_t s = (int64_t)g.rank * blockDim.x + threadIdx.x; s < nr; s += (int64_t)g.size * blockDim.x) {
+        const int64_t j = __ldcg(&ro[s]);
+        d.rphi[s] = polar_angle(rhat + j * m, m);
+        for (int k = 0; k < m; ++k) d.rsort[s * m + k] = rhat[j * m + k];
     }
 }
 

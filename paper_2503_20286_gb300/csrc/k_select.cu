@@ -229,21 +229,39 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_stats(Plan* plan)
 }
 
 // ------------------------------------------------------------ association
-// Error band of the FP32 projection scan, relative to |f|: covers the
-// rounding of f - z, 1/a, the product, the unit reference and the dot
-// product (<= (m + 8) u |f| each way), plus the FP64 rounding gap.
-__device__ __forceinline__ float assoc_band(float fnorm, int m) { return fnorm * (float)(2 * m + 40) * 0x1p-24f; }
+// FP32 scan: the perpendicular distance is computed in the cancellation-free
+// form d^2 = sum_k (f_k - g u_k)^2, g = f.u, u = r/|r| (linear in the angle
+// near the optimum, so its error band is narrow). Candidates come from the
+// angular index: references sorted by polar angle phi from axis 1; since the
+// angle between two directions is at least the difference of their polar
+// angles (triangle inequality on the sphere), only references with
+// |phi_r - phi_f| <= theta_best + margin can beat the best one found so far.
+// The scan walks outward from phi_f and stops on that bound.
+//
+// Error band of the FP32 distance (relative to |f|), two evaluations:
+// |delta d| <= (sqrt(m)(m + 10) + (m + 1)/2) u |f| each.
+__device__ __forceinline__ float assoc_band(int m)
+{
+    return (2.0f * sqrtf((float)m) * (float)(m + 10) + (float)(m + 8)) * 1.05f * 0x1p-24f;
+}
+// Extra angular margin of the index scan: covers the atan2/asin rounding and
+// keeps every unscanned reference farther than the band from the best.
+__device__ __forceinline__ float assoc_margin(int m) { return 1e-5f + 8.0f * assoc_band(m); }
+constexpr float kAssocMaxBound = 0.7853981f;  // beyond pi/4 the scan covers every reference
 
 template <int M>
-__device__ __forceinline__ void load_point32(const ProbDev& d, const Scal* sc, int64_t v, float* f, float& nrm)
+__device__ __forceinline__ float d2_f32(const float* f, const float* u)
 {
-    float s = 0.0f;
+    float g = f[0] * u[0];
+#pragma unroll
+    for (int k = 1; k < M; ++k) g = fmaf(f[k], u[k], g);
+    float d2 = 0.0f;
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-        f[k] = (d.in.F[v * M + k] - sc->z[k]) * sc->inv_a32[k];
-        s = fmaf(f[k], f[k], s);
+        const float e = fmaf(-g, u[k], f[k]);
+        d2 = fmaf(e, e, d2);
     }
-    nrm = sqrtf(s) * 1.0001f;
+    return d2;
 }
 
 // Exact decision between candidate references (FP64, reference formula).
@@ -261,12 +279,21 @@ __device__ inline void decide64(const ProbDev& d, const Scal* sc, int64_t v, int
     }
 }
 
+// First sorted position with rphi >= x.
+__device__ __forceinline__ int lower_bound_f(const float* a, int n, float x)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&a[mid]) < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <int M>
 __global__ void __launch_bounds__(256) k_assoc_m(Plan* plan, int pfirst, int plast)
 {
-    constexpr int P = 2;             // points per thread
-    constexpr int TR = 1024;         // references per shared-memory tile
-    __shared__ float s_r[TR * M];
     const int tid = threadIdx.x;
     for (int p = pfirst; p < plast; ++p) {
         const ProbDev& d = plan->p[p];
@@ -274,79 +301,79 @@ __global__ void __launch_bounds__(256) k_assoc_m(Plan* plan, int pfirst, int pla
         if (d.in.mode != MODE_SELECT || d.in.m != M || ld_volatile(&sc->status) != 0) continue;
         const int nS = ld_volatile(&sc->nS);
         const int nr = d.in.n_r;
-        const int per_block = 256 * P;
-        for (int64_t base = (int64_t)blockIdx.x * per_block; base < nS; base += (int64_t)gridDim.x * per_block) {
-            float f[P][M], nrm[P], b1[P], b2[P], b3[P];
-            int i1[P], i2[P];
-            int64_t v[P];
-            bool live[P];
+        const float* __restrict__ rphi = d.rphi;
+        const float* __restrict__ rs = d.rsort;
+        const int32_t* __restrict__ ro = d.rord + (int64_t)sc->rbuf * nr;
+        const float band = assoc_band(M), margin = assoc_margin(M);
+        for (int64_t s = (int64_t)blockIdx.x * 256 + tid; s < nS; s += (int64_t)gridDim.x * 256) {
+            const int64_t v = d.slist[s];
+            float f[M];
+            float n2 = 0.0f;
 #pragma unroll
-            for (int q = 0; q < P; ++q) {
-                const int64_t s = base + q * 256 + tid;
-                live[q] = s < nS;
-                v[q] = live[q] ? d.slist[s] : 0;
-                if (live[q]) load_point32<M>(d, sc, v[q], f[q], nrm[q]);
-                else {
-#pragma unroll
-                    for (int k = 0; k < M; ++k) f[q][k] = 0.0f;
-                    nrm[q] = 0.0f;
-                }
-                b1[q] = b2[q] = b3[q] = -INFINITY;
-                i1[q] = i2[q] = -1;
+            for (int k = 0; k < M; ++k) {
+                f[k] = (d.in.F[v * M + k] - sc->z[k]) * sc->inv_a32[k];
+                n2 = fmaf(f[k], f[k], n2);
             }
-            for (int t0 = 0; t0 < nr; t0 += TR) {
-                const int nt = min(TR, nr - t0);
-                __syncthreads();
-                for (int i = tid; i < nt * M; i += 256) s_r[i] = d.rhat[(int64_t)t0 * M + i];
-                __syncthreads();
-                for (int jj = 0; jj < nt; ++jj) {
-                    float r[M];
+            const float nrm = sqrtf(n2);
+            if (!(nrm > 0.0f) || !isfinite(nrm)) {  // at the ideal point (or overflow): exhaustive FP64 scan
+                const int slot = atomicAdd(&d.sc->nflag, 1);
+                d.flagged[slot] = (int32_t)v;
+                d.flagged_bound[slot] = INFINITY;
+                continue;
+            }
+            const float phif = polar_angle(f, M);
+            float c1 = INFINITY, c2 = INFINITY, c3 = INFINITY;  // FP32 d^2, best three
+            int s1 = -1, s2 = -1;                                 // sorted positions of the best two
+            float bound = INFINITY;                               // angular half-width still to scan
+            int L = lower_bound_f(rphi, nr, phif) - 1, Rp = L + 1;
+            while (L >= 0 || Rp < nr) {  // at most n_r steps
+                const float dl = L >= 0 ? phif - __ldg(&rphi[L]) : INFINITY;
+                const float dr = Rp < nr ? __ldg(&rphi[Rp]) - phif : INFINITY;
+                const bool left = L >= 0 && (Rp >= nr || dl <= dr);
+                const float dm = left ? dl : dr;
+                if (!(dm <= bound)) break;
+                const int q = left ? L-- : Rp++;  // 0 <= q < n_r
+                float u[M];
 #pragma unroll
-                    for (int k = 0; k < M; ++k) r[k] = s_r[jj * M + k];
-                    const int j = t0 + jj;
-#pragma unroll
-                    for (int q = 0; q < P; ++q) {
-                        float gq = f[q][0] * r[0];
-#pragma unroll
-                        for (int k = 1; k < M; ++k) gq = fmaf(f[q][k], r[k], gq);
-                        if (gq > b3[q]) {
-                            if (gq > b2[q]) {
-                                b3[q] = b2[q];
-                                if (gq > b1[q]) { b2[q] = b1[q]; i2[q] = i1[q]; b1[q] = gq; i1[q] = j; }
-                                else { b2[q] = gq; i2[q] = j; }
-                            } else {
-                                b3[q] = gq;
-                            }
-                        }
+                for (int k = 0; k < M; ++k) u[k] = __ldg(&rs[(int64_t)q * M + k]);
+                const float dd = d2_f32<M>(f, u);
+                if (dd < c3) {
+                    if (dd < c2) {
+                        c3 = c2;
+                        if (dd < c1) { c2 = c1; s2 = s1; c1 = dd; s1 = q; }
+                        else { c2 = dd; s2 = q; }
+                        // angle of the best so far, bounded from above
+                        const float sn = fminf(1.0f, sqrtf(c1) / nrm * 1.00001f + 2.0f * band);
+                        const float th = asinf(sn);
+                        bound = th + margin > kAssocMaxBound ? INFINITY : th + margin;
+                    } else {
+                        c3 = dd;
                     }
                 }
             }
-#pragma unroll
-            for (int q = 0; q < P; ++q) {
-                if (!live[q]) continue;
-                const float band = assoc_band(nrm[q], M);
-                const float lim = b1[q] - band;
-                int cand[2];
-                int nc = 0;
-                if ((b3[q] >= lim && nr > 2) || i1[q] < 0 || !isfinite(lim)) {
-                    const int slot = atomicAdd(&d.sc->nflag, 1);
-                    d.flagged[slot] = (int32_t)v[q];
-                    continue;
-                }
-                cand[nc++] = i1[q];
-                if (i2[q] >= 0 && b2[q] >= lim) cand[nc++] = i2[q];
-                int bj;
-                double bd2;
-                decide64(d, sc, v[q], M, cand, nc, bj, bd2);
-                d.pi[v[q]] = bj;
-                d.d64[v[q]] = __dsqrt_rn(bd2);
+            const float d1 = sqrtf(c1), lim = d1 + band * nrm;
+            if (sqrtf(c3) <= lim) {  // three or more references inside the band
+                const int slot = atomicAdd(&d.sc->nflag, 1);
+                d.flagged[slot] = (int32_t)v;
+                d.flagged_bound[slot] = bound;
+                continue;
             }
+            int cand[2];
+            int nc = 0;
+            cand[nc++] = __ldg(&ro[s1]);
+            if (s2 >= 0 && sqrtf(c2) <= lim) cand[nc++] = __ldg(&ro[s2]);
+            int bj;
+            double bd2;
+            decide64(d, sc, v, M, cand, nc, bj, bd2);
+            d.pi[v] = bj;
+            d.d64[v] = __dsqrt_rn(bd2);
         }
     }
 }
 
-// All-reference scan for points whose FP32 band holds three or more
-// references: one warp per point, exact FP64 over every candidate.
+// Points whose FP32 band holds three or more references: one warp per point
+// re-evaluates, in FP64, every reference of the scanned angular range whose
+// FP32 distance lies within the band of the range minimum.
 __global__ void __launch_bounds__(256) k_rescan(Plan* plan)
 {
     const int lane = threadIdx.x & 31;
@@ -358,33 +385,49 @@ __global__ void __launch_bounds__(256) k_rescan(Plan* plan)
         if (d.in.mode != MODE_SELECT || ld_volatile(&sc->status) != 0) continue;
         const int nflag = ld_volatile(&sc->nflag);
         const int m = d.in.m, nr = d.in.n_r;
+        const int32_t* ro = d.rord + (int64_t)sc->rbuf * nr;
+        const float band = assoc_band(m);
         for (int64_t w = gw; w < nflag; w += nw) {
             const int64_t v = d.flagged[w];
+            const float bound = d.flagged_bound[w];
             float f[kMaxM];
-            float s = 0.0f;
+            float n2 = 0.0f;
             for (int k = 0; k < m; ++k) {
                 f[k] = (d.in.F[v * m + k] - sc->z[k]) * sc->inv_a32[k];
-                s = fmaf(f[k], f[k], s);
+                n2 = fmaf(f[k], f[k], n2);
             }
-            const float band = assoc_band(sqrtf(s) * 1.0001f, m);
-            auto proj = [&](int j) {
-                const float* r = d.rhat + (int64_t)j * m;
-                float gq = f[0] * r[0];
-                for (int k = 1; k < m; ++k) gq = fmaf(f[k], r[k], gq);
-                return gq;
+            const float nrm = sqrtf(n2);
+            const bool all = !(bound < INFINITY) || !(nrm > 0.0f) || !isfinite(nrm);
+            int lo = 0, hi = nr;
+            if (!all) {
+                const float phif = polar_angle(f, m);
+                lo = lower_bound_f(d.rphi, nr, phif - bound);
+                hi = lower_bound_f(d.rphi, nr, nextafterf(phif + bound, INFINITY));
+            }
+            auto dist32 = [&](int q) {
+                const float* u = d.rsort + (int64_t)q * m;
+                float g = f[0] * u[0];
+                for (int k = 1; k < m; ++k) g = fmaf(f[k], u[k], g);
+                float d2 = 0.0f;
+                for (int k = 0; k < m; ++k) {
+                    const float e = fmaf(-g, u[k], f[k]);
+                    d2 = fmaf(e, e, d2);
+                }
+                return sqrtf(d2);
             };
-            float gmax = -INFINITY;
-            for (int j = lane; j < nr; j += 32) gmax = fmaxf(gmax, proj(j));
+            float dmin = INFINITY;
+            if (!all)
+                for (int q = lo + lane; q < hi; q += 32) dmin = fminf(dmin, dist32(q));
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-            const float lim = gmax - band;
+            for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+            const float lim = dmin + band * nrm;
             double fn[kMaxM];
             for (int k = 0; k < m; ++k) fn[k] = fnorm64(d.in.F[v * m + k], sc->z[k], sc->a[k]);
             double bd2 = INFINITY;
             int bj = INT32_MAX;
-            const bool all_refs = !isfinite(lim);  // overflowed projections: decide every reference in FP64
-            for (int j = lane; j < nr; j += 32) {
-                if (all_refs || proj(j) >= lim) {
+            for (int q = lo + lane; q < hi; q += 32) {
+                if (all || dist32(q) <= lim) {
+                    const int j = __ldg(&ro[q]);
                     const double d2 = perp_d2(fn, d.in.R + (int64_t)j * m, m);
                     if (d2 < bd2 || (d2 == bd2 && j < bj)) { bd2 = d2; bj = j; }
                 }
@@ -397,7 +440,7 @@ __global__ void __launch_bounds__(256) k_rescan(Plan* plan)
             }
             if (lane == 0) {
                 if (bj == INT32_MAX) {  // every distance was NaN
-                    set_status(d.sc, EMO_ERR_NONFINITE);
+                    set_status(sc, EMO_ERR_NONFINITE);
                     bj = 0;
                 }
                 d.pi[v] = bj;
@@ -413,7 +456,7 @@ cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, cudaSt
     for (int p = 0; p < nprob;) {
         int q = p;
         while (q < nprob && m_of[q] == m_of[p]) ++q;
-        const unsigned grid = (unsigned)sms * 4;
+        const unsigned grid = (unsigned)sms * 8;
         switch (m_of[p]) {
 #define X(MM) \
     case MM: k_assoc_m<MM><<<grid, 256, 0, s>>>(plan, p, q); break;

@@ -178,6 +178,23 @@ def test_zero_reference_rejected_on_device():
     assert info["status"] == 2
 
 
+def test_negative_reference_rejected_on_device():
+    F = wl.population(600, 3, 9, "sphere", seed=33)
+    R = wl.das_dennis(8, 3)
+    R[5, 1] = -0.25
+    s, info, _ = _gpu.gpu_select(F, R, 300, seed=1, debug=False)
+    assert info["status"] == 1
+
+
+@pytest.mark.parametrize("H", [300, 631])
+def test_select_many_references_angular_index(H):
+    """Large direction sets exercise the pruned angular scan of the
+    association (and the exhaustive FP64 scan of near ties)."""
+    F = wl.population(6000, 3, 12, "sphere", seed=40 + H)
+    R = wl.das_dennis(H, 3)
+    info, t = _gpu.compare_select(F, R, 3000, seed=H)
+
+
 def test_bounded_wait_times_out_and_context_survives():
     """A one-cycle budget makes every cross-CTA barrier give up: the call
     reports EMO_ERR_TIMEOUT through its status word instead of hanging, and
