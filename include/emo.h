@@ -165,6 +165,24 @@ size_t emo_batch_workspace_size(const emo_problem* descs, int32_t batch);
 emo_status emo_nsga3_select_batch(const emo_problem* descs, int32_t batch, void* ws,
                                   size_t ws_bytes, emo_stream_t stream);
 
+/*
+ * emo_nsga3_select without a caller workspace, for callers that cannot
+ * allocate device memory (a plug-in whose host owns every allocation, a loop
+ * that must not enter an allocator, a fixed memory budget). The paper has no
+ * counterpart; this is a deployment convenience. The selection runs in an
+ * 8 MiB scratch array built into the library (held on every GPU that loads
+ * it until the process exits); populations with n2 <= 8192 and n_r <= 8192
+ * (any m <= 16) always fit, larger ones return EMO_ERR_WORKSPACE. The call
+ * makes no device allocation. Its first call on a device looks up the
+ * scratch address (cudaGetSymbolAddress) and should come before any stream
+ * capture. Calls share the scratch: every call initialises what it reads,
+ * but calls that overlap on the GPU race and must be ordered by the caller.
+ * Other arguments as for emo_nsga3_select.
+ */
+emo_status emo_nsga3_select_noalloc(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
+                                    int64_t n_keep, uint64_t seed, uint64_t generation, int32_t* survivors,
+                                    emo_select_info* info, emo_stream_t stream);
+
 /* Synchronises `stream` and reads the device status word of a workspace
  * last used on it (EMO_OK when every problem finished cleanly). */
 emo_status emo_workspace_status(const void* ws, emo_stream_t stream, int32_t* status_out);

@@ -96,6 +96,8 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             L.emo_status_string.argtypes = [ctypes.c_int]
             L.emo_version.restype = i32
             L.emo_version.argtypes = []
+            L.emo_nsga3_select_noalloc.restype = ctypes.c_int
+            L.emo_nsga3_select_noalloc.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp, vp]
             L.emo_set_stage_timing.restype = None
             L.emo_set_stage_timing.argtypes = [i32]
             L.emo_stage_times.restype = i32
@@ -261,3 +263,19 @@ def emo_stage_times() -> list[tuple[str, float]]:
     if n < 0:
         raise EmoError(4, "emo_stage_times")
     return [(names[i].decode(), float(ms[i])) for i in range(n)]
+
+
+def emo_nsga3_select_noalloc(F: torch.Tensor, R: torch.Tensor, n_keep: int, seed: int = 0, generation: int = 0,
+                             survivors: torch.Tensor | None = None, info: torch.Tensor | None = None,
+                             stream=None):
+    """Selection in the library's built-in device scratch: for callers that
+    cannot allocate a workspace. ``survivors`` (and ``info``) may be given
+    pre-allocated; with them the call allocates no device memory at all."""
+    n2, m = F.shape
+    if survivors is None:
+        survivors = torch.empty(n_keep, dtype=torch.int32, device=F.device)
+    _check(lib().emo_nsga3_select_noalloc(_ptr(F), n2, m, _ptr(R), R.shape[0], n_keep,
+                                          seed & 0xFFFFFFFFFFFFFFFF, generation & 0xFFFFFFFFFFFFFFFF,
+                                          _ptr(survivors), _ptr(info), _stream(stream)),
+           "emo_nsga3_select_noalloc")
+    return survivors
