@@ -180,7 +180,7 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
         int q = p;
         long long hi = item;
         while (q < nprob && ins[q].m == ins[p].m) hi += dom_items_of(ins[q++].n2);
-        if (launch_dominance_tri_range(ins[p].m, plan, di.sms, s, item, hi, &plan->dom_ctr[ins[p].m]) !=
+        if (launch_dominance_tri_range(ins[p].m, plan, di.sms, s, item, hi, &plan->dom_ctr[ins[p].m], p, q) !=
             cudaSuccess)
             return EMO_ERR_CUDA;
         item = hi;

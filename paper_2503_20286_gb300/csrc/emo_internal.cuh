@@ -125,6 +125,7 @@ struct ProbDev {
     int32_t* elist;          // [n_r] references served in a level
     int32_t* flag;           // [n2] survivor flags / scan scratch
     int32_t* hist;           // [G][256] radix histograms, reused by the scans
+    unsigned char* colpre;   // [ncb][m-1] column-block prefix sets (colprep_obj_bytes each)
 };
 
 struct Plan {
@@ -162,6 +163,19 @@ __host__ __device__ __forceinline__ int64_t tiles_before(int64_t rb, int64_t ncb
 __host__ __device__ __forceinline__ int64_t tile_index(int64_t rb, int64_t cb, int64_t ncb)
 {
     return tiles_before(rb, ncb) + (cb - rb / 32);
+}
+
+// Column-block prefix sets of the dominance kernel. For each column block and
+// each key objective k (objectives 2..m), the block's 1024 columns sorted by
+// f_k descending (values and local indices), and the bitsets of the first
+// c * cps sorted columns for c = 0..1024/cps (checkpoints every cps columns).
+__host__ __device__ constexpr int colprep_log_cps(int K)
+{
+    return K <= 3 ? 1 : (K <= 5 ? 2 : (K <= 6 ? 3 : (K <= 9 ? 4 : 5)));
+}
+__host__ __device__ constexpr int64_t colprep_obj_bytes(int K)
+{
+    return kColBlock * 4 + kColBlock * 2 + ((kColBlock >> colprep_log_cps(K)) + 1) * 32 * 4;
 }
 
 // Byte layout of one problem region; fills `d` when base != 0. Returns the
@@ -206,6 +220,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         o_rsort = take(nr * m * 4);
         o_fbound = take(n2 * 4);
     }
+    int64_t o_colpre = take(ncb * (m - 1) * colprep_obj_bytes((int)(m - 1)));
     int64_t o_D = take(ntiles * 4096);
     if (base && d) {
         d->in = in;
@@ -241,6 +256,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         d->rphi = in.mode == MODE_SELECT ? (float*)(base + o_rphi) : nullptr;
         d->rsort = in.mode == MODE_SELECT ? (float*)(base + o_rsort) : nullptr;
         d->flagged_bound = in.mode == MODE_SELECT ? (float*)(base + o_fbound) : nullptr;
+        d->colpre = (unsigned char*)(base + o_colpre);
         d->D = (uint32_t*)(base + o_D);
     }
     return off;

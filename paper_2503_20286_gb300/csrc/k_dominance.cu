@@ -1,41 +1,52 @@
 // Pareto-dominance matrix kernels (Section III-C, Listing 1; Section IV-A;
 // Algorithm S.3 first two lines).
 //
-// k_dom_tri  -- selection path. Points are in lexicographic order, so for
-//   p < q only "p dominates q" is possible and it holds iff objectives
-//   2..m of p are <= those of q and the two points are not identical
-//   (objective 1 is ordered by the sort). One warp owns R row blocks, a lane
-//   owns one row and keeps its keys in registers; the 1024 column keys of the
-//   work item are staged in shared memory by a bulk-async copy and read as
-//   broadcasts. Each comparison result is OR-ed into the lane's word, so a
-//   lane ends with whole 32-bit words of its row. Finished 4 KB tiles are
-//   written from shared memory with bulk-async stores. The dominator count of
-//   every column (the column sum c_j of D) is accumulated from the staged
-//   tiles with a Harley-Seal bit-sliced vertical counter.
-// k_dom_full -- emo_dominance: every ordered pair in the caller's order,
-//   "all <= and some <" evaluated directly.
+// Selection path (points in lexicographic order, so for p < q only "p
+// dominates q" is possible; it holds iff f_k(q) >= f_k(p) for every key
+// objective k = 2..m and the points are not identical):
+//   k_colprep -- for each 1024-column block and key objective k, sorts the
+//     block's columns by f_k (descending) and stores, every CPS sorted
+//     columns, the bitset of the columns seen so far. The set
+//     {q in block : f_k(q) >= f_k(p)} is then a prefix of that order: a
+//     checkpoint bitset plus at most CPS - 1 extra bits.
+//   k_dom_pref<M> (m <= 6; k_dom_pref_rt for m >= 7) -- one warp per row block, lane = word of the 32-word row
+//     segment of a column block: for each row, count_ge by binary search (one
+//     lane per row), then the row's word = AND over k of the prefix bitsets,
+//     masked by q > p (diagonal blocks) and by the runs of identical points.
+//     Rows are stored as coalesced 128-byte segments of the tile; the
+//     dominator count of every column (column sums of D) is accumulated by a
+//     Harley-Seal bit-sliced counter per lane.
+// emo_dominance (caller order, full matrix): k_dom_full compares every
+//   ordered pair directly ("all <= and some <").
 #include "emo_kernels.cuh"
 
 namespace emo {
 
-template <int K>
-struct DomShape {
-    static constexpr int R = 2;   // row blocks per warp
-    static constexpr int NW = 8;  // warps per CTA
-    static constexpr int CB = K <= 2 ? 32 : (K <= 4 ? 16 : (K <= 8 ? 8 : 4));  // columns per register batch
-};
 constexpr int kDomNH = 8;  // high count planes: up to 4095 rows per lane and item
 constexpr long long kCopyWaitCycles = 1ll << 32;
 
+// Geometry of the per-objective prefix-set blocks (runtime form).
+struct PrefGeom {
+    int log_cps, cps, obj_bytes;
+    __device__ __forceinline__ explicit PrefGeom(int K)
+        : log_cps(colprep_log_cps(K)), cps(1 << colprep_log_cps(K)), obj_bytes((int)colprep_obj_bytes(K))
+    {
+    }
+};
+constexpr int kPrefOrdOff = kColBlock * 4;  // offsets inside one objective block
+constexpr int kPrefPbOff = kColBlock * 6;
+constexpr int kDomRtMaxK = kMaxM - 1;
+constexpr int kDomTemplMaxM = 6;            // fully unrolled kernels for m <= 6
+
 template <int K>
-struct DomSmem {
-    alignas(128) float ck[kColBlock * K];
-    alignas(128) int32_t rs[kColBlock];
-    alignas(128) uint32_t tiles[DomShape<K>::NW][DomShape<K>::R][kTileRows * kTileWords];
-    int32_t cnt[kColBlock];
-    uint64_t bar;
-    long long item;
-    int skip;
+struct PrefShape {
+    static constexpr int LOG_CPS = colprep_log_cps(K);
+    static constexpr int CPS = 1 << LOG_CPS;
+    static constexpr int NCP = (kColBlock >> LOG_CPS) + 1;  // checkpoints 0..1024/CPS
+    static constexpr int OBJ_BYTES = (int)colprep_obj_bytes(K);
+    static constexpr int SV_OFF = 0;                        // float   [1024] sorted values (desc)
+    static constexpr int ORD_OFF = kColBlock * 4;           // uint16  [1024] local column of each
+    static constexpr int PB_OFF = kColBlock * 6;            // uint32  [NCP][32] prefix bitsets
 };
 
 // Decode a dominance item of one problem: column blocks are served from the
@@ -65,24 +76,167 @@ __device__ __forceinline__ void flush_counts(VCount<NH>& vc, int32_t* s_cnt, int
     vc = VCount<NH>();
 }
 
-template <int M>
-__global__ void __launch_bounds__(256, 1) k_dom_tri(Plan* plan, long long item_lo, long long item_hi,
-                                                    unsigned long long* counter)
+// ------------------------------------------------------------ k_colprep
+__global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int plast)
 {
-    constexpr int K = M - 1;
-    using S = DomShape<K>;
-    constexpr int R = S::R, NW = S::NW, CB = S::CB;
+    __shared__ float s_v[kColBlock];
+    __shared__ uint16_t s_i[kColBlock];
+    __shared__ uint32_t s_part[8][32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int p = pfirst; p < plast; ++p) {
+        const ProbDev& d = plan->p[p];
+        if (ld_volatile(&d.sc->status) != 0) continue;
+        const int K = d.in.m - 1;
+        const PrefGeom G(K);
+        const int ncp1 = kColBlock >> G.log_cps;  // checkpoints after the first
+        const long long items = (long long)d.ncb * K;
+        for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+            const int cb = (int)(it / K), k = (int)(it % K);
+            unsigned char* blk = d.colpre + ((int64_t)cb * K + k) * G.obj_bytes;
+            for (int q = tid; q < kColBlock; q += blockDim.x) {
+                s_v[q] = d.keys[((int64_t)cb * kColBlock + q) * K + k];
+                s_i[q] = (uint16_t)q;
+            }
+            __syncthreads();
+            // bitonic sort: value descending, local index ascending on ties
+            for (int size = 2; size <= kColBlock; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int t = tid; t < kColBlock / 2; t += blockDim.x) {
+                        const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+                        const float vi = s_v[i], vj = s_v[j];
+                        const int ii = s_i[i], ij = s_i[j];
+                        const bool j_first = vj > vi || (vj == vi && ij < ii);
+                        const bool up = (i & size) == 0;
+                        if (up == j_first) {
+                            s_v[i] = vj; s_v[j] = vi;
+                            s_i[i] = (uint16_t)ij; s_i[j] = (uint16_t)ii;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            float* sv = reinterpret_cast<float*>(blk);
+            uint16_t* so = reinterpret_cast<uint16_t*>(blk + kPrefOrdOff);
+            uint32_t* pb = reinterpret_cast<uint32_t*>(blk + kPrefPbOff);
+            for (int q = tid; q < kColBlock; q += blockDim.x) {
+                sv[q] = s_v[q];
+                so[q] = s_i[q];
+            }
+            // prefix bitsets: warp w covers checkpoints (w*seg, (w+1)*seg]; lane = word
+            const int seg = ncp1 / 8;
+            uint32_t part = 0u;
+            for (int c = warp * seg; c < (warp + 1) * seg; ++c)
+                for (int e = 0; e < G.cps; ++e) {
+                    const int col = s_i[c * G.cps + e];
+                    if ((col >> 5) == lane) part |= 1u << (col & 31);
+                }
+            s_part[warp][lane] = part;
+            __syncthreads();
+            uint32_t acc = 0u;
+            for (int w = 0; w < warp; ++w) acc |= s_part[w][lane];
+            if (warp == 0) pb[lane] = 0u;
+            for (int c = warp * seg; c < (warp + 1) * seg; ++c) {
+                for (int e = 0; e < G.cps; ++e) {
+                    const int col = s_i[c * G.cps + e];
+                    if ((col >> 5) == lane) acc |= 1u << (col & 31);
+                }
+                pb[(c + 1) * 32 + lane] = acc;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------ k_dom_pref
+template <int K>
+struct PrefSmem {
+    alignas(128) unsigned char obj[K * PrefShape<K>::OBJ_BYTES];
+    alignas(128) int32_t rs[kColBlock];
+    int32_t cnt[kColBlock];
+    uint64_t bar;
+    long long item;
+    int skip;
+};
+
+// Number of entries >= x in a descending array of 1024 floats.
+__device__ __forceinline__ int count_ge(const float* sv, float x)
+{
+    int pos = 0;
+#pragma unroll
+    for (int step = 512; step > 0; step >>= 1)
+        if (sv[pos + step - 1] >= x) pos += step;
+    if (sv[pos] >= x) ++pos;
+    return pos;
+}
+
+// Words of the 32 rows of row block rb in column block cb (lane = word).
+// DIAG: the row block overlaps the column block (keep q > p only).
+// DUP: a run of identical points may reach into the column block.
+template <int K, bool DIAG, bool DUP>
+__device__ __forceinline__ void pref_rows(const unsigned char* __restrict__ obj, const int32_t* __restrict__ rs,
+                                          const int (&t)[K], int64_t rowbase, int64_t cbase, uint32_t* tile,
+                                          VCount<kDomNH>& vc, int lane)
+{
+    using S = PrefShape<K>;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        uint32_t x[16];
+#pragma unroll
+        for (int ii = 0; ii < 16; ++ii) {
+            const int i = h * 16 + ii;
+            uint32_t word = 0xFFFFFFFFu;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const unsigned char* ob = obj + k * S::OBJ_BYTES;
+                const int tk = __shfl_sync(0xffffffffu, t[k], i);
+                const int c = tk >> S::LOG_CPS;
+                uint32_t wk = reinterpret_cast<const uint32_t*>(ob + S::PB_OFF)[c * 32 + lane];
+                const int rem = tk & (S::CPS - 1);
+                const uint16_t* so = reinterpret_cast<const uint16_t*>(ob + S::ORD_OFF);
+#pragma unroll
+                for (int e = 0; e < S::CPS - 1; ++e) {
+                    const int col = so[min((c << S::LOG_CPS) + e, kColBlock - 1)];
+                    const bool hit = (e < rem) & ((col >> 5) == lane);
+                    wk |= hit ? (1u << (col & 31)) : 0u;
+                }
+                word &= wk;
+            }
+            const int64_t prow = rowbase + i;
+            if (DIAG) {
+                const int64_t off = prow - (cbase + 32 * lane);  // keep columns q > p
+                const int sh = (int)(off < 0 ? 0 : (off > 30 ? 31 : off + 1));  // shift count in [0, 31]
+                word &= off >= 31 ? 0u : (off >= 0 ? 0xFFFFFFFFu << sh : 0xFFFFFFFFu);
+            }
+            if (DUP) {
+                // identical points (same run) never dominate each other
+#pragma unroll 4
+                for (int bb = 0; bb < 32; ++bb) {
+                    const int b = (bb + lane) & 31;
+                    if ((int64_t)rs[32 * lane + b] <= prow) word &= ~(1u << b);
+                }
+            }
+            __stcs(&tile[i * 32 + (lane ^ i)], word);
+            x[ii] = word;
+        }
+        vc.add16(x);
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_lo, long long item_hi,
+                                                     unsigned long long* counter)
+{
+    constexpr int K = M - 1, NW = 16;
+    using S = PrefShape<K>;
     extern __shared__ __align__(128) unsigned char smraw[];
-    DomSmem<K>& sm = *reinterpret_cast<DomSmem<K>*>(smraw);
+    PrefSmem<K>& sm = *reinterpret_cast<PrefSmem<K>*>(smraw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) mbar_init(&sm.bar, 1);
     __syncthreads();
     uint32_t parity = 0;
 
     while (true) {
-        if (tid == 0) {
-            sm.item = item_lo + (long long)atomicAdd(counter, 1ull);
-        }
+        if (tid == 0) sm.item = item_lo + (long long)atomicAdd(counter, 1ull);
         __syncthreads();
         const long long item = sm.item;
         if (item >= item_hi) break;
@@ -95,14 +249,14 @@ __global__ void __launch_bounds__(256, 1) k_dom_tri(Plan* plan, long long item_l
             sm.skip = ld_volatile(&d.sc->status) != 0;
             if (!sm.skip) {
                 fence_proxy_async_smem();
+                const uint32_t ob = (uint32_t)(K * S::OBJ_BYTES);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&sm.bar)),
-                             "r"((uint32_t)(kColBlock * K * 4 + kColBlock * 4))
+                             "r"(ob + (uint32_t)(kColBlock * 4))
                              : "memory");
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(sm.ck)),
-                    "l"(d.keys + (int64_t)cb * kColBlock * K), "r"((uint32_t)(kColBlock * K * 4)),
-                    "r"(smem_u32(&sm.bar))
+                        smem_u32(sm.obj)),
+                    "l"(d.colpre + (int64_t)cb * K * S::OBJ_BYTES), "r"(ob), "r"(smem_u32(&sm.bar))
                     : "memory");
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -131,91 +285,35 @@ __global__ void __launch_bounds__(256, 1) k_dom_tri(Plan* plan, long long item_l
         const int64_t cbase = (int64_t)cb * kColBlock;
         VCount<kDomNH> vc;
 
-        for (int rbg = rb_lo + warp * R; rbg < rb_hi; rbg += NW * R) {
-            float rk[R][K];
-            int64_t prow[R];
-            bool rvalid[R], diag[R];
-            bool anydup = false;
+        // keys of the lane's row in the warp's first row block (prefetched
+        // one row block ahead)
+        float key[K];
+        {
+            const int64_t pl = (int64_t)(rb_lo + warp) * kTileRows + lane;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int rb = rbg + r;
-                rvalid[r] = rb < rb_hi;
-                prow[r] = (int64_t)rb * kTileRows + lane;
-                const bool live = rvalid[r] && prow[r] < n2;
+            for (int k = 0; k < K; ++k) key[k] = (rb_lo + warp < rb_hi && pl < n2) ? __ldg(&d.keys[pl * K + k]) : 0.0f;
+        }
+        for (int rb = rb_lo + warp; rb < rb_hi; rb += NW) {
+            const int64_t pl = (int64_t)rb * kTileRows + lane;
+            int t[K];
 #pragma unroll
-                for (int k = 0; k < K; ++k) rk[r][k] = live ? __ldg(&d.keys[prow[r] * K + k]) : INFINITY;
-                diag[r] = rvalid[r] && (int64_t)rb * kTileRows + 31 >= cbase;
-                anydup |= rvalid[r] && rb * kTileRows + 31 >= dupcut;
+            for (int k = 0; k < K; ++k) {
+                const float* sv = reinterpret_cast<const float*>(sm.obj + k * S::OBJ_BYTES + S::SV_OFF);
+                t[k] = pl < n2 ? count_ge(sv, key[k]) : 0;
             }
-            for (int w = 0; w < kTileWords; ++w) {
-                uint32_t wd[R];
+            {
+                const int rbn = rb + NW;
+                const int64_t pn = (int64_t)rbn * kTileRows + lane;
 #pragma unroll
-                for (int r = 0; r < R; ++r) wd[r] = 0u;
-#pragma unroll
-                for (int cc = 0; cc < 32; cc += CB) {
-                    float ck[CB * K];
-                    const float4* src = reinterpret_cast<const float4*>(sm.ck + (w * 32 + cc) * K);
-#pragma unroll
-                    for (int v = 0; v < CB * K / 4; ++v) {
-                        float4 t = src[v];
-                        ck[4 * v + 0] = t.x;
-                        ck[4 * v + 1] = t.y;
-                        ck[4 * v + 2] = t.z;
-                        ck[4 * v + 3] = t.w;
-                    }
-#pragma unroll
-                    for (int b = 0; b < CB; ++b) {
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            bool le = rk[r][0] <= ck[b * K + 0];
-#pragma unroll
-                            for (int k = 1; k < K; ++k) le = le & (rk[r][k] <= ck[b * K + k]);
-                            if (le) wd[r] |= 1u << (cc + b);
-                        }
-                    }
-                }
-                if (anydup) {
-                    // identical points (same run) never dominate each other
-                    for (int b = 0; b < 32; ++b) {
-                        const int rs = sm.rs[w * 32 + b];
-#pragma unroll
-                        for (int r = 0; r < R; ++r)
-                            if ((int64_t)rs <= prow[r]) wd[r] &= ~(1u << b);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (diag[r]) {
-                        const int64_t off = prow[r] - (cbase + 32 * w);  // keep columns q > p
-                        if (off >= 31) wd[r] = 0u;
-                        else if (off >= 0) wd[r] &= 0xFFFFFFFFu << (off + 1);
-                    }
-                    sm.tiles[warp][r][lane * 32 + (w ^ lane)] = wd[r];
-                }
+                for (int k = 0; k < K; ++k) key[k] = (rbn < rb_hi && pn < n2) ? __ldg(&d.keys[pn * K + k]) : 0.0f;
             }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (rvalid[r]) {
-                        uint32_t* dst = d.D + tile_index(rbg + r, cb, d.ncb) * (int64_t)(kTileRows * kTileWords);
-                        bulk_store(dst, sm.tiles[warp][r], kTileRows * kTileWords * 4);
-                    }
-                bulk_commit();
-            }
-            // column counts from the staged tiles: lane = word column
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (!rvalid[r]) continue;
-                uint32_t x[32];
-#pragma unroll
-                for (int row = 0; row < 32; ++row) x[row] = sm.tiles[warp][r][row * 32 + (lane ^ row)];
-                vc.add16(x);
-                vc.add16(x + 16);
-            }
-            if (lane == 0) bulk_wait_read_all();
-            __syncwarp();
+            const bool diag = (int64_t)rb * kTileRows + 31 >= cbase;
+            const bool dup = rb * kTileRows + 31 >= dupcut;
+            const int64_t rowbase = (int64_t)rb * kTileRows;
+            uint32_t* tile = d.D + tile_index(rb, cb, d.ncb) * (int64_t)(kTileRows * kTileWords);
+            if (dup) pref_rows<K, true, true>(sm.obj, sm.rs, t, rowbase, cbase, tile, vc, lane);
+            else if (diag) pref_rows<K, true, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vc, lane);
+            else pref_rows<K, false, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vc, lane);
         }
         flush_counts(vc, sm.cnt, lane);
         __syncthreads();
@@ -225,7 +323,133 @@ __global__ void __launch_bounds__(256, 1) k_dom_tri(Plan* plan, long long item_l
         }
         __syncthreads();
     }
-    if (lane == 0) bulk_wait_all();
+}
+
+// Runtime-K variant for m >= 7 (compact code: loops over the key objectives
+// are not unrolled; the ranks of a row block are staged in shared memory).
+__global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long item_lo, long long item_hi,
+                                                        unsigned long long* counter, int K)
+{
+    constexpr int NW = 16;
+    const PrefGeom G(K);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    const int obj_total = K * G.obj_bytes;
+    unsigned char* obj = smraw;
+    int32_t* rs = reinterpret_cast<int32_t*>(smraw + ((obj_total + 127) & ~127));
+    int32_t* cnt = rs + kColBlock;
+    int32_t* st = cnt + kColBlock;  // [NW][K][32] ranks of the warp's row block
+    uint64_t* bar = reinterpret_cast<uint64_t*>(st + NW * K * 32);
+    long long* s_item = reinterpret_cast<long long*>(bar + 1);
+    int* s_skip = reinterpret_cast<int*>(s_item + 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int32_t* myst = st + warp * K * 32;
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    uint32_t parity = 0;
+
+    while (true) {
+        if (tid == 0) *s_item = item_lo + (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long item = *s_item;
+        if (item >= item_hi) break;
+        int p = 0;
+        while (p + 1 < plan->nprob && plan->dom_item_start[p + 1] <= item) ++p;
+        const ProbDev& d = plan->p[p];
+        int cb, chunk;
+        dom_decode(item - plan->dom_item_start[p], d.ncb, d.nrb, cb, chunk);
+        if (tid == 0) {
+            *s_skip = ld_volatile(&d.sc->status) != 0 || d.in.m - 1 != K;
+            if (!*s_skip) {
+                fence_proxy_async_smem();
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                             "r"((uint32_t)obj_total + (uint32_t)(kColBlock * 4))
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(obj)),
+                    "l"(d.colpre + (int64_t)cb * obj_total), "r"((uint32_t)obj_total), "r"(smem_u32(bar))
+                    : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(rs)),
+                    "l"(d.runstart + (int64_t)cb * kColBlock), "r"((uint32_t)(kColBlock * 4)), "r"(smem_u32(bar))
+                    : "memory");
+            }
+        }
+        for (int i = tid; i < kColBlock; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        if (*s_skip) continue;
+        if (!mbar_wait(bar, parity, kCopyWaitCycles)) {
+            if (tid == 0) set_status(d.sc, EMO_ERR_TIMEOUT);
+            mbar_wait(bar, parity, kCopyWaitCycles);
+            break;
+        }
+        parity ^= 1u;
+
+        const int64_t n2 = d.in.n2;
+        const int rbmax = min(d.nrb, 32 * (cb + 1));
+        const int rb_lo = chunk * kDomRowChunk, rb_hi = min(rbmax, rb_lo + kDomRowChunk);
+        const int dupcut = d.minrs[cb];
+        const int64_t cbase = (int64_t)cb * kColBlock;
+        VCount<kDomNH> vc;
+        for (int rb = rb_lo + warp; rb < rb_hi; rb += NW) {
+            const int64_t pl = (int64_t)rb * kTileRows + lane;
+            for (int k = 0; k < K; ++k) {
+                const float* sv = reinterpret_cast<const float*>(obj + k * G.obj_bytes);
+                myst[k * 32 + lane] = pl < n2 ? count_ge(sv, __ldg(&d.keys[pl * K + k])) : 0;
+            }
+            __syncwarp();
+            const bool diag = (int64_t)rb * kTileRows + 31 >= cbase;
+            const bool dup = rb * kTileRows + 31 >= dupcut;
+            uint32_t* tile = d.D + tile_index(rb, cb, d.ncb) * (int64_t)(kTileRows * kTileWords);
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                uint32_t x[16];
+#pragma unroll
+                for (int ii = 0; ii < 16; ++ii) {
+                    const int i = h * 16 + ii;
+                    uint32_t word = 0xFFFFFFFFu;
+#pragma unroll 1
+                    for (int k = 0; k < K; ++k) {
+                        const unsigned char* ob = obj + k * G.obj_bytes;
+                        const int tk = myst[k * 32 + i];
+                        const int c = tk >> G.log_cps;
+                        uint32_t wk = reinterpret_cast<const uint32_t*>(ob + kPrefPbOff)[c * 32 + lane];
+                        const int rem = tk & (G.cps - 1);
+                        const uint16_t* so = reinterpret_cast<const uint16_t*>(ob + kPrefOrdOff) + (c << G.log_cps);
+                        for (int e = 0; e < rem; ++e) {
+                            const int col = so[e];
+                            if ((col >> 5) == lane) wk |= 1u << (col & 31);
+                        }
+                        word &= wk;
+                    }
+                    const int64_t prow = (int64_t)rb * kTileRows + i;
+                    if (diag) {
+                        const int64_t off = prow - (cbase + 32 * lane);
+                        if (off >= 31) word = 0u;
+                        else if (off >= 0) word &= 0xFFFFFFFFu << (int)(off + 1);
+                    }
+                    if (dup && word) {
+                        for (int bb = 0; bb < 32; ++bb) {
+                            const int b = (bb + lane) & 31;
+                            if ((int64_t)rs[32 * lane + b] <= prow) word &= ~(1u << b);
+                        }
+                    }
+                    __stcs(&tile[i * 32 + (lane ^ i)], word);
+                    x[ii] = word;
+                }
+                vc.add16(x);
+            }
+            __syncwarp();
+        }
+        flush_counts(vc, cnt, lane);
+        __syncthreads();
+        for (int q = tid; q < kColBlock; q += blockDim.x) {
+            const int c = cnt[(q & 31) * 32 + (q >> 5)];
+            if (c) atomicAdd(&d.cnt[cbase + q], c);
+        }
+        __syncthreads();
+    }
 }
 
 // Full matrix in caller order: D_ij = all(F_i <= F_j) and any(F_i < F_j).
@@ -328,16 +552,33 @@ template <int M>
 static cudaError_t launch_tri_m(Plan* plan, int sms, cudaStream_t s, long long lo, long long hi,
                                 unsigned long long* counter)
 {
-    const size_t smem = sizeof(DomSmem<M - 1>);
-    cudaError_t e = cudaFuncSetAttribute(k_dom_tri<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sizeof(PrefSmem<M - 1>);
+    cudaError_t e = cudaFuncSetAttribute(k_dom_pref<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dom_tri<M>, 256, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dom_pref<M>, 512, smem);
     if (e != cudaSuccess) return e;
     long long grid = (long long)sms * (occ > 0 ? occ : 1);
     if (grid > hi - lo) grid = hi - lo;
     if (grid < 1) return cudaSuccess;
-    k_dom_tri<M><<<(unsigned)grid, 256, smem, s>>>(plan, lo, hi, counter);
+    k_dom_pref<M><<<(unsigned)grid, 512, smem, s>>>(plan, lo, hi, counter);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_tri_rt(int K, Plan* plan, int sms, cudaStream_t s, long long lo, long long hi,
+                                 unsigned long long* counter)
+{
+    const int obj_total = K * (int)colprep_obj_bytes(K);
+    const size_t smem = (size_t)((obj_total + 127) & ~127) + 2 * kColBlock * 4 + 16 * K * 32 * 4 + 64;
+    cudaError_t e = cudaFuncSetAttribute(k_dom_pref_rt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dom_pref_rt, 512, smem);
+    if (e != cudaSuccess) return e;
+    long long grid = (long long)sms * (occ > 0 ? occ : 1);
+    if (grid > hi - lo) grid = hi - lo;
+    if (grid < 1) return cudaSuccess;
+    k_dom_pref_rt<<<(unsigned)grid, 512, smem, s>>>(plan, lo, hi, counter, K);
     return cudaGetLastError();
 }
 
@@ -363,14 +604,20 @@ static cudaError_t launch_full_m(const float* F, int64_t n2, uint32_t* D, int64_
 // The plan's problems are ordered by m; items of objective count m form one
 // contiguous range served by the m-instantiation.
 cudaError_t launch_dominance_tri_range(int m, Plan* plan, int sms, cudaStream_t s, long long lo, long long hi,
-                                       unsigned long long* counter)
+                                       unsigned long long* counter, int pfirst, int plast)
 {
+    k_colprep<<<sms * 4, 256, 0, s>>>(plan, pfirst, plast);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     switch (m) {
-#define X(MM) \
-    case MM: return launch_tri_m<MM>(plan, sms, s, lo, hi, counter);
-        EMO_FOR_EACH_M(X)
-#undef X
-    default: return cudaErrorInvalidValue;
+    case 2: return launch_tri_m<2>(plan, sms, s, lo, hi, counter);
+    case 3: return launch_tri_m<3>(plan, sms, s, lo, hi, counter);
+    case 4: return launch_tri_m<4>(plan, sms, s, lo, hi, counter);
+    case 5: return launch_tri_m<5>(plan, sms, s, lo, hi, counter);
+    case 6: return launch_tri_m<6>(plan, sms, s, lo, hi, counter);
+    default:
+        if (m < 2 || m > kMaxM) return cudaErrorInvalidValue;
+        return launch_tri_rt(m - 1, plan, sms, s, lo, hi, counter);
     }
 }
 
