@@ -197,6 +197,12 @@ const char* emo_status_string(int status);
 /* Library version, e.g. 100 for 0.1.0. */
 int32_t emo_version(void);
 
+/* Human-readable report of the current device as the library sees it (SM
+ * count, cooperative-launch support, registers, shared memory and resident
+ * CTAs of the cooperative kernels) into buf (NUL-terminated, truncated to
+ * len). Returns the full report length, -1 on bad arguments. */
+int32_t emo_device_report(char* buf, int32_t len);
+
 /* Opt-in stage timing for profiling. While enabled, every multi-stage call
  * records CUDA events on its stream between its stages (prep, sort,
  * dominance, peel, stats, assoc, rescan, csr, niche, finish). After a call,

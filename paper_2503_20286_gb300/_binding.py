@@ -98,6 +98,8 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             L.emo_version.argtypes = []
             L.emo_nsga3_select_noalloc.restype = ctypes.c_int
             L.emo_nsga3_select_noalloc.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp, vp]
+            L.emo_device_report.restype = i32
+            L.emo_device_report.argtypes = [ctypes.c_char_p, i32]
             L.emo_set_stage_timing.restype = None
             L.emo_set_stage_timing.argtypes = [i32]
             L.emo_stage_times.restype = i32
@@ -279,3 +281,9 @@ def emo_nsga3_select_noalloc(F: torch.Tensor, R: torch.Tensor, n_keep: int, seed
                                           _ptr(survivors), _ptr(info), _stream(stream)),
            "emo_nsga3_select_noalloc")
     return survivors
+
+
+def emo_device_report() -> str:
+    buf = ctypes.create_string_buffer(4096)
+    lib().emo_device_report(buf, 4096)
+    return buf.value.decode()

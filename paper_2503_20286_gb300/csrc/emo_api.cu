@@ -3,7 +3,9 @@
 // call synchronises except emo_workspace_status.
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
 #include <cstdlib>
+#include <string>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -15,6 +17,7 @@ using namespace emo;
 namespace {
 
 std::atomic<long long> g_spin_budget{0};
+constexpr int kPeelDynSmem = peel_smem_bytes((int)(kMaxN2 / kColBlock));
 std::atomic<int> g_timing{0};
 
 // Per-thread stage timing of the last run() (opt-in; events on the launch stream).
@@ -88,13 +91,17 @@ DevInfo dev_info()
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return DevInfo{};
         if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
             return DevInfo{};
+        if (cudaFuncSetAttribute((const void*)k_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeelDynSmem) !=
+            cudaSuccess)
+            return DevInfo{};
         int occ = 2;
+        // k_peel takes peel_smem_bytes(ncb) of dynamic shared memory, the others none
         const void* kernels[] = {(const void*)k_sort, (const void*)k_peel, (const void*)k_stats,
                                  (const void*)k_csr, (const void*)k_finish};
-        for (const void* k : kernels) {
+        const int dyn[] = {0, kPeelDynSmem, 0, 0, 0};
+        for (int i = 0; i < 5; ++i) {
             int o = 0;
-            // k_peel takes up to 8 KB of dynamic shared memory
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, kCoopThreads, 8192) != cudaSuccess)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernels[i], kCoopThreads, dyn[i]) != cudaSuccess)
                 return DevInfo{};
             occ = std::min(occ, o);
         }
@@ -187,8 +194,7 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
         p = q;
     }
     sm.mark("dominance");
-    const size_t peel_smem = (size_t)(max_ncb + 1) * sizeof(int);
-    if (peel_smem > 48 * 1024) return EMO_ERR_INVALID_ARG;
+    const size_t peel_smem = (size_t)peel_smem_bytes(max_ncb);
     if (coop((const void*)k_peel, di.G, peel_smem, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("peel");
     if (any_select) {
@@ -358,6 +364,36 @@ const char* emo_status_string(int status)
 }
 
 int32_t emo_version(void) { return 100; }
+
+int32_t emo_device_report(char* buf, int32_t len)
+{
+    if (!buf || len < 1) return -1;
+    std::string out;
+    int dev = -1, sms = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    out += "device " + std::to_string(dev) + (e == cudaSuccess ? "" : std::string(" error ") + cudaGetErrorString(e));
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    out += "; sms " + std::to_string(sms) + "; cooperative " + std::to_string(coop);
+    DevInfo di = dev_info();  // also sets the dynamic shared memory limit of k_peel
+    struct K { const char* name; const void* fn; int dyn; };
+    const K ks[] = {{"k_sort", (const void*)k_sort, 0}, {"k_peel", (const void*)k_peel, kPeelDynSmem},
+                    {"k_stats", (const void*)k_stats, 0}, {"k_csr", (const void*)k_csr, 0},
+                    {"k_finish", (const void*)k_finish, 0}};
+    for (const K& k : ks) {
+        cudaFuncAttributes fa{};
+        int occ = -1;
+        cudaError_t e1 = cudaFuncGetAttributes(&fa, k.fn);
+        cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, kCoopThreads, k.dyn);
+        out += std::string("; ") + k.name + " regs " + std::to_string(fa.numRegs) + " smem " +
+               std::to_string(fa.sharedSizeBytes) + " occ " + std::to_string(occ);
+        if (e1 != cudaSuccess || e2 != cudaSuccess)
+            out += std::string(" (") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2) + ")";
+    }
+    out += "; coop grid " + std::to_string(di.G) + (di.ok ? "" : " (unavailable)");
+    std::snprintf(buf, (size_t)len, "%s", out.c_str());
+    return (int32_t)out.size();
+}
 
 void emo_set_stage_timing(int32_t enable) { g_timing.store(enable ? 1 : 0); }
 

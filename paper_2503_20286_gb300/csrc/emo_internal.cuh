@@ -105,8 +105,8 @@ struct ProbDev {
     int32_t* cnt;            // [n2p] dominator counts (sorted order)
     int32_t* rank_s;         // [n2p] ranks (sorted order)
     int32_t* rank_o;         // [n2]  ranks (caller order)
-    int32_t* front;          // [2][n2p] front members grouped by column block
-    int32_t* front_n;        // [2][ncb] members per column block
+    int32_t* front;          // [3][n2p] front members grouped by column block (3 buffers)
+    int32_t* front_n;        // [3][ncb] members per column block
     int32_t* slist;          // [n2] caller indices of S = {rank <= l}
     int32_t* pi;             // [n2] associated reference
     double* d64;             // [n2] perpendicular distance (FP64)
@@ -196,8 +196,8 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
     int64_t o_cnt = take(n2p * 4);
     int64_t o_rank_s = take(n2p * 4);
     int64_t o_rank_o = take(n2 * 4);
-    int64_t o_front = take(2 * n2p * 4);
-    int64_t o_front_n = take(2 * ncb * 4);
+    int64_t o_front = take(3 * n2p * 4);
+    int64_t o_front_n = take(3 * ncb * 4);
     int64_t o_slist = take(n2 * 4);
     int64_t o_hist = take(int64_t(G) * kRadix * 4);
     int64_t o_flag = take((n2p + 1) * 4);

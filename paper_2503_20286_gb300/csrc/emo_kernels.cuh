@@ -102,6 +102,27 @@ struct VCount {
             c = t;
         }
     }
+    // Eight words at once (carry-save tree into the fours plane and below,
+    // eights carry rippled into the higher planes).
+    __device__ __forceinline__ void add8(const uint32_t* x)
+    {
+        uint32_t twosA, twosB, foursA, foursB, eightsA;
+        csa(twosA, ones, ones, x[0], x[1]);
+        csa(twosB, ones, ones, x[2], x[3]);
+        csa(foursA, twos, twos, twosA, twosB);
+        csa(twosA, ones, ones, x[4], x[5]);
+        csa(twosB, ones, ones, x[6], x[7]);
+        csa(foursB, twos, twos, twosA, twosB);
+        csa(eightsA, fours, fours, foursA, foursB);
+        uint32_t c = eightsA, t;
+        t = eights & c; eights ^= c; c = t;
+#pragma unroll
+        for (int i = 0; i < NH; ++i) {
+            t = hi[i] & c;
+            hi[i] ^= c;
+            c = t;
+        }
+    }
     __device__ __forceinline__ void add1(uint32_t x)
     {
         uint32_t c = x, t;
@@ -137,6 +158,9 @@ __global__ void k_setup(SetupArgs a, Plan* plan, char* ws);
 __global__ void k_prep(Plan* plan);
 __global__ void k_sort(Plan* plan);
 __global__ void k_peel(Plan* plan);
+
+// Dynamic shared memory of k_peel for ncb column blocks.
+__host__ __device__ constexpr int peel_smem_bytes(int ncb) { return (ncb + 1) * (int)sizeof(int); }
 __global__ void k_stats(Plan* plan);
 __global__ void k_rescan(Plan* plan);
 __global__ void k_csr(Plan* plan);

@@ -9,15 +9,26 @@ namespace emo {
 // One LSD pass over idx_src[0..n) -> idx_dst, digit = (key(v) >> shift) & 255.
 // Returns false when the group failed. Sets `skipped` when every element has
 // the same digit (the pass would not move anything).
+// Shared-memory scratch of radix_pass; declared once by the calling kernel
+// (a function-scope __shared__ array in a template would be duplicated per
+// key function).
+struct RadixSmem {
+    int hist[kRadix];
+    int off[kRadix];
+    int wc[kCoopThreads / 32][kRadix];
+    int tot[kRadix];
+    int skip;
+};
+
 template <typename KeyFn>
 __device__ bool radix_pass(const ProbDev& d, const Group& g, int gs, long long budget, int64_t n,
-                           const int32_t* src, int32_t* dst, int shift, KeyFn key, bool& skipped)
+                           const int32_t* src, int32_t* dst, int shift, KeyFn key, bool& skipped, RadixSmem& rsm)
 {
-    __shared__ int s_hist[kRadix];
-    __shared__ int s_off[kRadix];
-    __shared__ int s_wc[kCoopThreads / 32][kRadix];
-    __shared__ int s_tot[kRadix];
-    __shared__ int s_skip;
+    int* s_hist = rsm.hist;
+    int* s_off = rsm.off;
+    int (*s_wc)[kRadix] = rsm.wc;
+    int* s_tot = rsm.tot;
+    int& s_skip = rsm.skip;
     const int tid = threadIdx.x, warp = tid >> 5;
     const bool active = g.rank < gs;
     const int64_t chunk = cdiv(n, gs);

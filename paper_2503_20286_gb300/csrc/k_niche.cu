@@ -50,13 +50,14 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_csr(Plan* plan)
     int bits = 1;
     while ((1ll << bits) < (long long)nr) ++bits;
     int buf = 0;
+    __shared__ RadixSmem rsm;
     const int gs = (int)max((int64_t)1, min((int64_t)g.size, cdiv(nL, 4096)));
     for (int shift = 0; shift < bits; shift += kRadixBits) {
         const int32_t* src = d.llist + (int64_t)buf * n2;
         int32_t* dst = d.llist + (int64_t)(buf ^ 1) * n2;
         bool skipped = false;
         auto key = [&](int32_t v) { return (uint32_t)__ldcg(&d.pi[v]); };
-        if (!radix_pass(d, g, gs, budget, nL, src, dst, shift, key, skipped)) return;
+        if (!radix_pass(d, g, gs, budget, nL, src, dst, shift, key, skipped, rsm)) return;
         if (!skipped) buf ^= 1;
     }
     const int32_t* L = d.llist + (int64_t)buf * n2;

@@ -79,7 +79,7 @@ __global__ void k_prep(Plan* plan)
         d.flag[s] = 0;
     }
     for (int64_t i = tid; i < n2; i += stride) d.rank_o[i] = kNotRanked;
-    for (int64_t c = tid; c < 2 * (int64_t)d.ncb; c += stride) d.front_n[c] = 0;
+    for (int64_t c = tid; c < 3 * (int64_t)d.ncb; c += stride) d.front_n[c] = 0;
     for (int64_t c = tid; c < d.ncb; c += stride) d.minrs[c] = INT32_MAX;
     if (in.mode == MODE_SELECT) {
         for (int64_t j = tid; j < in.n_r; j += stride) {
@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
     const int m = in.m;
     const int gs = (int)max((int64_t)1, min((int64_t)g.size, cdiv(n2, 4096)));
     const float* F = in.F;
+    __shared__ RadixSmem rsm;
 
     int buf = 0;
     for (int k = m - 1; k >= 0; --k) {
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
             int32_t* dst = d.idx + (int64_t)(buf ^ 1) * d.n2p;
             bool skipped = false;
             auto key = [&](int32_t v) { return float_key(__ldg(&F[(int64_t)v * m + k])); };
-            if (!radix_pass(d, g, gs, budget, n2, src, dst, shift, key, skipped)) return;
+            if (!radix_pass(d, g, gs, budget, n2, src, dst, shift, key, skipped, rsm)) return;
             if (!skipped) buf ^= 1;
         }
     }
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
     for (int shift = 0; shift < 32; shift += kRadixBits) {
         bool skipped = false;
         if (!radix_pass(d, g, gr, budget, nr, d.rord + (int64_t)rb * nr, d.rord + (int64_t)(rb ^ 1) * nr, shift, rkey,
-                        skipped))
+                        skipped, rsm))
             return;
         if (!skipped) rb ^= 1;
     }
