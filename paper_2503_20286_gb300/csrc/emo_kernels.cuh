@@ -144,6 +144,29 @@ struct VCount {
         for (int i = 0; i < NH; ++i) a |= hi[i];
         return a != 0;
     }
+    // Highest plane index (0-based, over ones..hi[NH-1]) holding a set bit
+    // in any lane of the warp, -1 when all counters are zero.
+    __device__ __forceinline__ int top_plane() const
+    {
+        int t = -1;
+        if (ones) t = 0;
+        if (twos) t = 1;
+        if (fours) t = 2;
+        if (eights) t = 3;
+#pragma unroll
+        for (int i = 0; i < NH; ++i)
+            if (hi[i]) t = 4 + i;
+        return __reduce_max_sync(0xffffffffu, (unsigned)(t + 1)) - 1;
+    }
+    // Count of bit b using only planes 0..top.
+    __device__ __forceinline__ int count_upto(int b, int top) const
+    {
+        int c = ((ones >> b) & 1) | (((twos >> b) & 1) << 1) | (((fours >> b) & 1) << 2) | (((eights >> b) & 1) << 3);
+#pragma unroll
+        for (int i = 0; i < NH; ++i)
+            if (4 + i <= top) c |= ((hi[i] >> b) & 1) << (4 + i);
+        return c;
+    }
     __device__ __forceinline__ int count(int b) const
     {
         int c = ((ones >> b) & 1) | (((twos >> b) & 1) << 1) | (((fours >> b) & 1) << 2) | (((eights >> b) & 1) << 3);
@@ -159,8 +182,9 @@ __global__ void k_prep(Plan* plan);
 __global__ void k_sort(Plan* plan);
 __global__ void k_peel(Plan* plan);
 
+constexpr int kPeelChunk = 8192;   // front members staged in shared memory at once
 // Dynamic shared memory of k_peel for ncb column blocks.
-__host__ __device__ constexpr int peel_smem_bytes(int ncb) { return (ncb + 1) * (int)sizeof(int); }
+__host__ __device__ constexpr int peel_smem_bytes(int ncb) { return (ncb + 1 + kPeelChunk) * (int)sizeof(int); }
 __global__ void k_stats(Plan* plan);
 __global__ void k_rescan(Plan* plan);
 __global__ void k_csr(Plan* plan);

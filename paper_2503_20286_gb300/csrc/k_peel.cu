@@ -4,12 +4,14 @@
 //
 // One cooperative launch per call. Each CTA of a problem's group owns whole
 // column blocks (1024 sorted points) and their counts. Per front, the CTA
-// reads, for every member p of the front, the 128-byte segment of row p
-// that falls in its column block (one coalesced 4-byte load per lane), and
-// adds the words into per-lane Harley-Seal bit-sliced counters, giving d_j.
-// Points whose count reaches zero form the next front. One bounded group
-// barrier separates fronts. Selection stops once the fronts peeled hold
-// n_keep points (that front is l); ranking may continue to the end.
+// stages the members whose rows reach its blocks in shared memory, then for
+// every member reads the 128-byte segment of row p that falls in a block it
+// owns (one coalesced 4-byte load per lane; the next 16 members' loads are
+// in flight while the current 16 are counted) and adds the words into
+// per-lane Harley-Seal bit-sliced counters, giving d_j. Points whose count
+// reaches zero form the next front. One bounded group barrier separates
+// fronts. Selection stops once the fronts peeled hold n_keep points (that
+// front is l); ranking may continue to the end.
 #include "emo_kernels.cuh"
 
 namespace emo {
@@ -22,7 +24,8 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
     __shared__ int s_cnt[kColBlock];
     __shared__ int s_newn;
     __shared__ int s_warp[33];
-    extern __shared__ int s_pref[];  // [ncb + 1] prefix of front sizes per column block
+    extern __shared__ int s_dyn[];  // [ncb + 1] member prefix per block, [kPeelChunk] staged members
+    int* s_pref = s_dyn;
 
     const Group g = group_of(plan);
     const ProbDev& d = plan->p[g.prob];
@@ -32,6 +35,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n2 = in.n2, n2p = d.n2p;
     const int ncb = d.ncb;
+    int* s_mem = s_dyn + ncb + 1;
     const int64_t target = in.n_keep > 0 ? in.n_keep : n2;
 
     // ---- front 0: points without dominators
@@ -67,9 +71,9 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
         int32_t* fw = d.front + (int64_t)nxt * n2p;
         int32_t* fwn = d.front_n + (int64_t)nxt * ncb;
 
-        // prefix of the member counts of every column block
-        int last_cb = g.rank + ((ncb - 1 - g.rank) / g.size) * g.size;
-        if (g.rank < ncb) {
+        // prefix of the member counts of every column block up to the last owned one
+        const int last_cb = g.rank < ncb ? g.rank + ((ncb - 1 - g.rank) / g.size) * g.size : -1;
+        if (last_cb >= 0) {
             int run = 0;
             for (int base = 0; base <= last_cb; base += blockDim.x) {
                 const int c = base + tid;
@@ -83,64 +87,94 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
             if (tid == 0) s_pref[last_cb + 1] = run;
             __syncthreads();
         }
+        const int nall = last_cb >= 0 ? s_pref[last_cb + 1] : 0;  // members reaching the last owned block
 
-        for (int cb = g.rank; cb < ncb; cb += g.size) {
-            for (int q = tid; q < kColBlock; q += blockDim.x) s_cnt[q] = 0;
-            if (tid == 0) s_newn = 0;
+        for (int m0 = 0; m0 < nall; m0 += kPeelChunk) {
+            const int mc = min(kPeelChunk, nall - m0);
             __syncthreads();
-            const int nmem = s_pref[cb + 1];  // members in column blocks 0..cb
-            VCount<kPeelNH> vc;
-            for (int b0 = warp * 16; b0 < nmem; b0 += NW * 16) {
-                // lanes 0..15 locate members b0 .. b0 + 15
-                int pj = -1;
-                if (lane < 16 && b0 + lane < nmem) {
-                    const int o = b0 + lane;
-                    int lo = 0, hi = cb;  // segment with s_pref[seg] <= o < s_pref[seg + 1]
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_pref[mid] <= o) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    pj = __ldcg(&fr[(int64_t)lo * kColBlock + (o - s_pref[lo])]);
+            for (int i = tid; i < mc; i += blockDim.x) {  // stage members m0 .. m0 + mc in block order
+                const int o = m0 + i;
+                int lo = 0, hi = last_cb;  // block with s_pref[blk] <= o < s_pref[blk + 1]
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_pref[mid] <= o) lo = mid;
+                    else hi = mid - 1;
                 }
-                uint32_t x[16];
+                // stage (tile base of the member's row block, row): tile (rb, cb) is base + cb
+                const int p = __ldcg(&fr[(int64_t)lo * kColBlock + (o - s_pref[lo])]);
+                const int rb = p >> 5;
+                const uint32_t base = (uint32_t)(tiles_before(rb, ncb) - rb / 32);
+                s_mem[i] = (int)(base * 32u + (uint32_t)(p & 31));
+            }
+            __syncthreads();
+            for (int cb = g.rank; cb < ncb; cb += g.size) {
+                const int nmem = min(mc, s_pref[cb + 1] - m0);  // staged members reaching cb
+                if (nmem <= 0) continue;
+                for (int q = tid; q < kColBlock; q += blockDim.x) s_cnt[q] = 0;
+                if (tid == 0) s_newn = 0;
+                __syncthreads();
+                VCount<kPeelNH> vc;
+                auto load16 = [&](int b0, uint32_t (&x)[16]) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int p = __shfl_sync(0xffffffffu, pj, j);
-                    x[j] = 0u;
-                    if (p >= 0) {
-                        const int64_t t = tile_index(p >> 5, cb, ncb);
-                        x[j] = __ldcs(&d.D[t * (kTileRows * kTileWords) + (p & 31) * 32 + (lane ^ (p & 31))]);
+                    for (int j = 0; j < 16; ++j) {
+                        const int i = b0 + j;
+                        x[j] = 0u;
+                        if (i < nmem) {
+                            const uint32_t e = (uint32_t)s_mem[i];
+                            const uint32_t r = e & 31u;
+                            const int64_t t = (int64_t)(e >> 5) + cb;
+                            x[j] = __ldcs(&d.D[(t << 10) + (r << 5) + (lane ^ r)]);
+                        }
+                    }
+                };
+                uint32_t xa[16], xb[16];
+                int b0 = warp * 16;
+                if (b0 < nmem) load16(b0, xa);
+                while (b0 < nmem) {
+                    const int b1 = b0 + NW * 16;
+                    if (b1 < nmem) load16(b1, xb);  // next batch in flight while this one is counted
+                    vc.add16(xa);
+                    b0 = b1;
+                    if (b0 >= nmem) break;
+                    const int b2 = b0 + NW * 16;
+                    if (b2 < nmem) load16(b2, xa);
+                    vc.add16(xb);
+                    b0 = b2;
+                }
+                const int top = vc.top_plane();
+                if (top >= 0) {
+                    for (int b = 0; b < 32; ++b) {
+                        const int c = vc.count_upto(b, top);
+                        if (c) atomicAdd(&s_cnt[b * 32 + lane], c);
                     }
                 }
-                vc.add16(x);
-            }
-            if (__any_sync(0xffffffffu, vc.any())) {
-                for (int b = 0; b < 32; ++b) {
-                    const int c = vc.count(b);
-                    if (c) atomicAdd(&s_cnt[b * 32 + lane], c);
-                }
-            }
-            __syncthreads();
-            for (int q = tid; q < kColBlock; q += blockDim.x) {
-                const int dq = s_cnt[(q & 31) * 32 + (q >> 5)];
-                const int64_t s = (int64_t)cb * kColBlock + q;
-                if (dq && s < n2) {
-                    const int c = d.cnt[s] - dq;
-                    d.cnt[s] = c;
-                    if (c == 0) {
-                        const int slot = atomicAdd(&s_newn, 1);
-                        fw[(int64_t)cb * kColBlock + slot] = (int32_t)s;
-                        d.rank_s[s] = k + 1;
+                __syncthreads();
+                for (int q = tid; q < kColBlock; q += blockDim.x) {
+                    const int dq = s_cnt[(q & 31) * 32 + (q >> 5)];
+                    const int64_t s = (int64_t)cb * kColBlock + q;
+                    if (dq && s < n2) {
+                        const int c = d.cnt[s] - dq;
+                        d.cnt[s] = c;
+                        if (c == 0) {
+                            const int slot = atomicAdd(&s_newn, 1);
+                            fw[(int64_t)cb * kColBlock + slot] = (int32_t)s;
+                            d.rank_s[s] = k + 1;
+                        }
                     }
                 }
-            }
-            __syncthreads();
-            if (tid == 0) {
-                fwn[cb] = s_newn;
-                atomicAdd(&d.sc->ranked, s_newn);
+                __syncthreads();
+                if (tid == 0) {
+                    // counts of one block may arrive over several member chunks
+                    const int before = m0 == 0 ? 0 : fwn[cb];
+                    fwn[cb] = before + s_newn;
+                    atomicAdd(&d.sc->ranked, s_newn);
+                }
             }
         }
+        // blocks that received no member in this front still need their count of new members
+        if (tid == 0)
+            for (int cb = g.rank; cb < ncb; cb += g.size)
+                if (nall == 0 || s_pref[cb + 1] == 0) fwn[cb] = 0;
         if (!group_sync(d.sc, g.size, budget)) return;
         prev_total = total;
         total = ld_volatile(&d.sc->ranked);

@@ -201,6 +201,9 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
     // reference directions in order of their polar angle from axis 1 (the
     // index of the association scan)
     if (in.mode != MODE_SELECT) return;
+    // every CTA has read the run-start carries from d.hist before the radix
+    // passes below reuse it
+    if (!group_sync(d.sc, g.size, budget)) return;
     const int nr = in.n_r;
     const int gr = (int)max((int64_t)1, min((int64_t)g.size, cdiv(nr, 4096)));
     const float* rhat = d.rhat;
