@@ -205,7 +205,7 @@ int32_t emo_device_report(char* buf, int32_t len);
 
 /* Opt-in stage timing for profiling. While enabled, every multi-stage call
  * records CUDA events on its stream between its stages (prep, sort,
- * dominance, peel, stats, assoc, rescan, csr, niche, finish). After a call,
+ * colprep, dominance, peel, stats, assoc, rescan, csr, niche, finish). After a call,
  * emo_stage_times synchronises on the last event and writes up to max_n
  * stage durations (ms, host array) and static stage names (host array of
  * const char*, nullable). Returns the number of stages, 0 when nothing was

@@ -181,6 +181,8 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
     sm.mark("prep");
     if (coop((const void*)k_sort, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("sort");
+    if (launch_colprep(plan, di.sms, s, nprob) != cudaSuccess) return EMO_ERR_CUDA;
+    sm.mark("colprep");
     // dominance: one launch per objective count present
     long long item = 0;
     for (int p = 0; p < nprob;) {

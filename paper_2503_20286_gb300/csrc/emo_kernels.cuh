@@ -196,6 +196,7 @@ __global__ void k_finish(Plan* plan);
 cudaError_t launch_dominance_tri_range(int m, Plan* plan, int sms, cudaStream_t s, long long lo, long long hi,
                                        unsigned long long* counter, int pfirst, int plast);
 cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, cudaStream_t s);
+cudaError_t launch_colprep(Plan* plan, int sms, cudaStream_t s, int nprob);
 cudaError_t launch_dominance_full_c(const float* F, int64_t n2, int m, uint32_t* D, int64_t ld, int32_t* cnt,
                                     int sms, cudaStream_t s);
 

@@ -603,12 +603,17 @@ static cudaError_t launch_full_m(const float* F, int64_t n2, uint32_t* D, int64_
 
 // The plan's problems are ordered by m; items of objective count m form one
 // contiguous range served by the m-instantiation.
+cudaError_t launch_colprep(Plan* plan, int sms, cudaStream_t s, int nprob)
+{
+    k_colprep<<<sms * 4, 256, 0, s>>>(plan, 0, nprob);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dominance_tri_range(int m, Plan* plan, int sms, cudaStream_t s, long long lo, long long hi,
                                        unsigned long long* counter, int pfirst, int plast)
 {
-    k_colprep<<<sms * 4, 256, 0, s>>>(plan, pfirst, plast);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    (void)pfirst;
+    (void)plast;
     switch (m) {
     case 2: return launch_tri_m<2>(plan, sms, s, lo, hi, counter);
     case 3: return launch_tri_m<3>(plan, sms, s, lo, hi, counter);
