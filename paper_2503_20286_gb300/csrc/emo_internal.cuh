@@ -165,17 +165,21 @@ __host__ __device__ __forceinline__ int64_t tile_index(int64_t rb, int64_t cb, i
     return tiles_before(rb, ncb) + (cb - rb / 32);
 }
 
-// Column-block prefix sets of the dominance kernel. For each column block and
-// each key objective k (objectives 2..m), the block's 1024 columns sorted by
-// f_k descending (values and local indices), and the bitsets of the first
-// c * cps sorted columns for c = 0..1024/cps (checkpoints every cps columns).
+// Column-block prefix sets of the dominance kernel. Each 1024-column block
+// is split into two halves of 512 columns. For each half and key objective k
+// (objectives 2..m): the half's columns sorted by f_k descending (values and
+// local indices), and the bitsets of the first c * cps sorted columns of the
+// half for c = 0..512/cps. The bitsets of both halves are interleaved: row c
+// holds 32 words, words 0-15 from half 0 and 16-31 from half 1, so the word w
+// of a tile row always comes from half w / 16.
+//   per objective: float sv[2][512] | uint16 ord[2][512] | uint32 pb[512/cps + 1][32]
 __host__ __device__ constexpr int colprep_log_cps(int K)
 {
-    return K <= 3 ? 1 : (K <= 5 ? 2 : (K <= 6 ? 3 : (K <= 9 ? 4 : 5)));
+    return K <= 3 ? 0 : (K <= 5 ? 1 : (K <= 6 ? 2 : (K <= 9 ? 3 : 4)));
 }
 __host__ __device__ constexpr int64_t colprep_obj_bytes(int K)
 {
-    return kColBlock * 4 + kColBlock * 2 + ((kColBlock >> colprep_log_cps(K)) + 1) * 32 * 4;
+    return kColBlock * 4 + kColBlock * 2 + (((kColBlock / 2) >> colprep_log_cps(K)) + 1) * 32 * 4;
 }
 
 // Byte layout of one problem region; fills `d` when base != 0. Returns the

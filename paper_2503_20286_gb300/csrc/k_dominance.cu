@@ -4,18 +4,21 @@
 // Selection path (points in lexicographic order, so for p < q only "p
 // dominates q" is possible; it holds iff f_k(q) >= f_k(p) for every key
 // objective k = 2..m and the points are not identical):
-//   k_colprep -- for each 1024-column block and key objective k, sorts the
-//     block's columns by f_k (descending) and stores, every CPS sorted
-//     columns, the bitset of the columns seen so far. The set
-//     {q in block : f_k(q) >= f_k(p)} is then a prefix of that order: a
-//     checkpoint bitset plus at most CPS - 1 extra bits.
-//   k_dom_pref<M> (m <= 6; k_dom_pref_rt for m >= 7) -- one warp per row block, lane = word of the 32-word row
-//     segment of a column block: for each row, count_ge by binary search (one
-//     lane per row), then the row's word = AND over k of the prefix bitsets,
-//     masked by q > p (diagonal blocks) and by the runs of identical points.
-//     Rows are stored as coalesced 128-byte segments of the tile; the
-//     dominator count of every column (column sums of D) is accumulated by a
-//     Harley-Seal bit-sliced counter per lane.
+//   k_colprep -- for each 1024-column block, each half of 512 columns and
+//     each key objective k, sorts the half's columns by f_k (descending) and
+//     stores, every CPS sorted columns, the bitset of the columns seen so far.
+//     The set {q in half : f_k(q) >= f_k(p)} is then a prefix of that order:
+//     a checkpoint bitset plus at most CPS - 1 extra bits (CPS = 1 for m <= 4,
+//     so no extra bits at all).
+//   k_dom_pref<M> (m <= 6; k_dom_pref_rt for m >= 7) -- one warp per row
+//     block, lane = word of the 32-word row segment of a column block (lanes
+//     0-15 in half 0, 16-31 in half 1): each lane first counts, for its row
+//     and each objective, the columns of both halves that are >= (binary
+//     search); then, row by row, the word is the AND over the objectives of
+//     the prefix bitsets, masked by q > p (diagonal blocks) and by the runs of
+//     identical points. Rows are stored as coalesced 128-byte segments of the
+//     tile; the dominator count of every column (column sums of D) is
+//     accumulated by a Harley-Seal bit-sliced counter per lane.
 // emo_dominance (caller order, full matrix): k_dom_full compares every
 //   ordered pair directly ("all <= and some <").
 #include "emo_kernels.cuh"
@@ -24,6 +27,7 @@ namespace emo {
 
 constexpr int kDomNH = 8;  // high count planes: up to 4095 rows per lane and item
 constexpr long long kCopyWaitCycles = 1ll << 32;
+constexpr int kHalf = kColBlock / 2;
 
 // Geometry of the per-objective prefix-set blocks (runtime form).
 struct PrefGeom {
@@ -35,18 +39,12 @@ struct PrefGeom {
 };
 constexpr int kPrefOrdOff = kColBlock * 4;  // offsets inside one objective block
 constexpr int kPrefPbOff = kColBlock * 6;
-constexpr int kDomRtMaxK = kMaxM - 1;
-constexpr int kDomTemplMaxM = 6;            // fully unrolled kernels for m <= 6
 
 template <int K>
 struct PrefShape {
     static constexpr int LOG_CPS = colprep_log_cps(K);
     static constexpr int CPS = 1 << LOG_CPS;
-    static constexpr int NCP = (kColBlock >> LOG_CPS) + 1;  // checkpoints 0..1024/CPS
     static constexpr int OBJ_BYTES = (int)colprep_obj_bytes(K);
-    static constexpr int SV_OFF = 0;                        // float   [1024] sorted values (desc)
-    static constexpr int ORD_OFF = kColBlock * 4;           // uint16  [1024] local column of each
-    static constexpr int PB_OFF = kColBlock * 6;            // uint32  [NCP][32] prefix bitsets
 };
 
 // Decode a dominance item of one problem: column blocks are served from the
@@ -88,7 +86,7 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
         if (ld_volatile(&d.sc->status) != 0) continue;
         const int K = d.in.m - 1;
         const PrefGeom G(K);
-        const int ncp1 = kColBlock >> G.log_cps;  // checkpoints after the first
+        const int ncp1 = kHalf >> G.log_cps;  // checkpoints after the first
         const long long items = (long long)d.ncb * K;
         for (long long it = blockIdx.x; it < items; it += gridDim.x) {
             const int cb = (int)(it / K), k = (int)(it % K);
@@ -98,14 +96,16 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
                 s_i[q] = (uint16_t)q;
             }
             __syncthreads();
-            // bitonic sort: value descending, local index ascending on ties
+            // bitonic sort: half ascending, then value descending, then local
+            // index ascending (positions 0..511 = half 0, 512..1023 = half 1)
             for (int size = 2; size <= kColBlock; size <<= 1) {
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
                     for (int t = tid; t < kColBlock / 2; t += blockDim.x) {
                         const int i = 2 * t - (t & (stride - 1)), j = i + stride;
                         const float vi = s_v[i], vj = s_v[j];
                         const int ii = s_i[i], ij = s_i[j];
-                        const bool j_first = vj > vi || (vj == vi && ij < ii);
+                        const int hi_ = ii >= kHalf, hj = ij >= kHalf;
+                        const bool j_first = hj < hi_ || (hj == hi_ && (vj > vi || (vj == vi && ij < ii)));
                         const bool up = (i & size) == 0;
                         if (up == j_first) {
                             s_v[i] = vj; s_v[j] = vi;
@@ -122,12 +122,14 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
                 sv[q] = s_v[q];
                 so[q] = s_i[q];
             }
-            // prefix bitsets: warp w covers checkpoints (w*seg, (w+1)*seg]; lane = word
+            // interleaved prefix bitsets: lane w builds word w from the sorted
+            // columns of half w / 16; warp v covers checkpoints (v*seg, (v+1)*seg]
+            const int hbase = (lane >> 4) * kHalf;
             const int seg = ncp1 / 8;
             uint32_t part = 0u;
             for (int c = warp * seg; c < (warp + 1) * seg; ++c)
                 for (int e = 0; e < G.cps; ++e) {
-                    const int col = s_i[c * G.cps + e];
+                    const int col = s_i[hbase + c * G.cps + e];
                     if ((col >> 5) == lane) part |= 1u << (col & 31);
                 }
             s_part[warp][lane] = part;
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
             if (warp == 0) pb[lane] = 0u;
             for (int c = warp * seg; c < (warp + 1) * seg; ++c) {
                 for (int e = 0; e < G.cps; ++e) {
-                    const int col = s_i[c * G.cps + e];
+                    const int col = s_i[hbase + c * G.cps + e];
                     if ((col >> 5) == lane) acc |= 1u << (col & 31);
                 }
                 pb[(c + 1) * 32 + lane] = acc;
@@ -158,15 +160,44 @@ struct PrefSmem {
     int skip;
 };
 
-// Number of entries >= x in a descending array of 1024 floats.
-__device__ __forceinline__ int count_ge(const float* sv, float x)
+// Number of entries >= x in a descending array of 512 floats.
+__device__ __forceinline__ int count_ge512(const float* sv, float x)
 {
     int pos = 0;
 #pragma unroll
-    for (int step = 512; step > 0; step >>= 1)
+    for (int step = 256; step > 0; step >>= 1)
         if (sv[pos + step - 1] >= x) pos += step;
     if (sv[pos] >= x) ++pos;
     return pos;
+}
+
+// Packed counts of both halves of one objective: t0 | t1 << 16.
+__device__ __forceinline__ int count_ge_halves(const unsigned char* ob, float x)
+{
+    const float* sv = reinterpret_cast<const float*>(ob);
+    return count_ge512(sv, x) | (count_ge512(sv + kHalf, x) << 16);
+}
+
+// Word of objective k's prefix set for the lane (packed half counts t01).
+template <int LOG_CPS>
+__device__ __forceinline__ uint32_t prefix_word(const unsigned char* ob, int t01, int lane)
+{
+    const int half = lane >> 4;
+    const int t = (t01 >> (16 * half)) & 0xFFFF;
+    const int c = t >> LOG_CPS;
+    uint32_t w = reinterpret_cast<const uint32_t*>(ob + kPrefPbOff)[c * 32 + lane];
+    if (LOG_CPS > 0) {
+        constexpr int CPS = 1 << LOG_CPS;
+        const int rem = t & (CPS - 1);
+        const uint16_t* so = reinterpret_cast<const uint16_t*>(ob + kPrefOrdOff) + half * kHalf;
+#pragma unroll
+        for (int e = 0; e < CPS - 1; ++e) {
+            const int col = so[min((c << LOG_CPS) + e, kHalf - 1)];
+            const bool hit = (e < rem) & ((col >> 5) == lane);
+            w |= hit ? (1u << (col & 31)) : 0u;
+        }
+    }
+    return w;
 }
 
 // Words of the 32 rows of row block rb in column block cb (lane = word).
@@ -186,21 +217,8 @@ __device__ __forceinline__ void pref_rows(const unsigned char* __restrict__ obj,
             const int i = h * 16 + ii;
             uint32_t word = 0xFFFFFFFFu;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const unsigned char* ob = obj + k * S::OBJ_BYTES;
-                const int tk = __shfl_sync(0xffffffffu, t[k], i);
-                const int c = tk >> S::LOG_CPS;
-                uint32_t wk = reinterpret_cast<const uint32_t*>(ob + S::PB_OFF)[c * 32 + lane];
-                const int rem = tk & (S::CPS - 1);
-                const uint16_t* so = reinterpret_cast<const uint16_t*>(ob + S::ORD_OFF);
-#pragma unroll
-                for (int e = 0; e < S::CPS - 1; ++e) {
-                    const int col = so[min((c << S::LOG_CPS) + e, kColBlock - 1)];
-                    const bool hit = (e < rem) & ((col >> 5) == lane);
-                    wk |= hit ? (1u << (col & 31)) : 0u;
-                }
-                word &= wk;
-            }
+            for (int k = 0; k < K; ++k)
+                word &= prefix_word<S::LOG_CPS>(obj + k * S::OBJ_BYTES, __shfl_sync(0xffffffffu, t[k], i), lane);
             const int64_t prow = rowbase + i;
             if (DIAG) {
                 const int64_t off = prow - (cbase + 32 * lane);  // keep columns q > p
@@ -220,6 +238,62 @@ __device__ __forceinline__ void pref_rows(const unsigned char* __restrict__ obj,
         }
         vc.add16(x);
     }
+}
+
+// Stage the prefix sets of column block cb (and its run starts); returns
+// false when the problem is skipped or the copy timed out.
+__device__ __forceinline__ bool dom_stage(const ProbDev& d, int cb, int K, int obj_bytes, unsigned char* obj,
+                                          int32_t* rs, int32_t* cnt, uint64_t* bar, int* s_skip, uint32_t& parity,
+                                          bool& fatal)
+{
+    const int tid = threadIdx.x;
+    const uint32_t ob = (uint32_t)(K * obj_bytes);
+    if (tid == 0) {
+        *s_skip = ld_volatile(&d.sc->status) != 0 || d.in.m - 1 != K;
+        if (!*s_skip) {
+            fence_proxy_async_smem();
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                         "r"(ob + (uint32_t)(kColBlock * 4))
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(obj)),
+                "l"(d.colpre + (int64_t)cb * ob), "r"(ob), "r"(smem_u32(bar))
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(rs)),
+                "l"(d.runstart + (int64_t)cb * kColBlock), "r"((uint32_t)(kColBlock * 4)), "r"(smem_u32(bar))
+                : "memory");
+        }
+    }
+    for (int i = tid; i < kColBlock; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    if (*s_skip) return false;
+    // The copy is a local load that always completes; the bound only guards
+    // against a lost completion. On timeout the status is set and the CTA
+    // still waits (bounded) so that no copy is in flight at exit.
+    if (!mbar_wait(bar, parity, kCopyWaitCycles)) {
+        if (tid == 0) set_status(d.sc, EMO_ERR_TIMEOUT);
+        mbar_wait(bar, parity, kCopyWaitCycles);
+        fatal = true;
+        return false;
+    }
+    parity ^= 1u;
+    return true;
+}
+
+// Column counts of the item: smem reduction, one global atomic per column.
+__device__ __forceinline__ void dom_flush_item(const ProbDev& d, int64_t cbase, VCount<kDomNH>& vc, int32_t* cnt,
+                                               int lane)
+{
+    flush_counts(vc, cnt, lane);
+    __syncthreads();
+    for (int q = threadIdx.x; q < kColBlock; q += blockDim.x) {
+        const int c = cnt[(q & 31) * 32 + (q >> 5)];
+        if (c) atomicAdd(&d.cnt[cbase + q], c);
+    }
+    __syncthreads();
 }
 
 template <int M>
@@ -245,39 +319,11 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
         const ProbDev& d = plan->p[p];
         int cb, chunk;
         dom_decode(item - plan->dom_item_start[p], d.ncb, d.nrb, cb, chunk);
-        if (tid == 0) {
-            sm.skip = ld_volatile(&d.sc->status) != 0;
-            if (!sm.skip) {
-                fence_proxy_async_smem();
-                const uint32_t ob = (uint32_t)(K * S::OBJ_BYTES);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&sm.bar)),
-                             "r"(ob + (uint32_t)(kColBlock * 4))
-                             : "memory");
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(sm.obj)),
-                    "l"(d.colpre + (int64_t)cb * K * S::OBJ_BYTES), "r"(ob), "r"(smem_u32(&sm.bar))
-                    : "memory");
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(sm.rs)),
-                    "l"(d.runstart + (int64_t)cb * kColBlock), "r"((uint32_t)(kColBlock * 4)), "r"(smem_u32(&sm.bar))
-                    : "memory");
-            }
+        bool fatal = false;
+        if (!dom_stage(d, cb, K, S::OBJ_BYTES, sm.obj, sm.rs, sm.cnt, &sm.bar, &sm.skip, parity, fatal)) {
+            if (fatal) break;
+            continue;
         }
-        for (int i = tid; i < kColBlock; i += blockDim.x) sm.cnt[i] = 0;
-        __syncthreads();
-        if (sm.skip) continue;
-        // The copy is a local load that always completes; the bound only
-        // guards against a lost completion. On timeout the status is set and
-        // the CTA still waits (bounded) so that no copy is in flight at exit.
-        if (!mbar_wait(&sm.bar, parity, kCopyWaitCycles)) {
-            if (tid == 0) set_status(d.sc, EMO_ERR_TIMEOUT);
-            mbar_wait(&sm.bar, parity, kCopyWaitCycles);
-            break;
-        }
-        parity ^= 1u;
-
         const int64_t n2 = d.in.n2;
         const int rbmax = min(d.nrb, 32 * (cb + 1));
         const int rb_lo = chunk * kDomRowChunk, rb_hi = min(rbmax, rb_lo + kDomRowChunk);
@@ -285,8 +331,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
         const int64_t cbase = (int64_t)cb * kColBlock;
         VCount<kDomNH> vc;
 
-        // keys of the lane's row in the warp's first row block (prefetched
-        // one row block ahead)
+        // keys of the lane's row in the warp's next row block (prefetched)
         float key[K];
         {
             const int64_t pl = (int64_t)(rb_lo + warp) * kTileRows + lane;
@@ -297,10 +342,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
             const int64_t pl = (int64_t)rb * kTileRows + lane;
             int t[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const float* sv = reinterpret_cast<const float*>(sm.obj + k * S::OBJ_BYTES + S::SV_OFF);
-                t[k] = pl < n2 ? count_ge(sv, key[k]) : 0;
-            }
+            for (int k = 0; k < K; ++k) t[k] = pl < n2 ? count_ge_halves(sm.obj + k * S::OBJ_BYTES, key[k]) : 0;
             {
                 const int rbn = rb + NW;
                 const int64_t pn = (int64_t)rbn * kTileRows + lane;
@@ -315,18 +357,13 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
             else if (diag) pref_rows<K, true, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vc, lane);
             else pref_rows<K, false, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vc, lane);
         }
-        flush_counts(vc, sm.cnt, lane);
-        __syncthreads();
-        for (int q = tid; q < kColBlock; q += blockDim.x) {
-            const int c = sm.cnt[(q & 31) * 32 + (q >> 5)];
-            if (c) atomicAdd(&d.cnt[cbase + q], c);
-        }
-        __syncthreads();
+        dom_flush_item(d, cbase, vc, sm.cnt, lane);
     }
 }
 
 // Runtime-K variant for m >= 7 (compact code: loops over the key objectives
-// are not unrolled; the ranks of a row block are staged in shared memory).
+// are not unrolled; the packed half counts of a row block are staged in
+// shared memory).
 __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long item_lo, long long item_hi,
                                                         unsigned long long* counter, int K)
 {
@@ -337,12 +374,13 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
     unsigned char* obj = smraw;
     int32_t* rs = reinterpret_cast<int32_t*>(smraw + ((obj_total + 127) & ~127));
     int32_t* cnt = rs + kColBlock;
-    int32_t* st = cnt + kColBlock;  // [NW][K][32] ranks of the warp's row block
+    int32_t* st = cnt + kColBlock;  // [NW][K][32] packed half counts of the warp's row block
     uint64_t* bar = reinterpret_cast<uint64_t*>(st + NW * K * 32);
     long long* s_item = reinterpret_cast<long long*>(bar + 1);
     int* s_skip = reinterpret_cast<int*>(s_item + 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int32_t* myst = st + warp * K * 32;
+    const int half = lane >> 4;
     if (tid == 0) mbar_init(bar, 1);
     __syncthreads();
     uint32_t parity = 0;
@@ -357,35 +395,11 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
         const ProbDev& d = plan->p[p];
         int cb, chunk;
         dom_decode(item - plan->dom_item_start[p], d.ncb, d.nrb, cb, chunk);
-        if (tid == 0) {
-            *s_skip = ld_volatile(&d.sc->status) != 0 || d.in.m - 1 != K;
-            if (!*s_skip) {
-                fence_proxy_async_smem();
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                             "r"((uint32_t)obj_total + (uint32_t)(kColBlock * 4))
-                             : "memory");
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(obj)),
-                    "l"(d.colpre + (int64_t)cb * obj_total), "r"((uint32_t)obj_total), "r"(smem_u32(bar))
-                    : "memory");
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(rs)),
-                    "l"(d.runstart + (int64_t)cb * kColBlock), "r"((uint32_t)(kColBlock * 4)), "r"(smem_u32(bar))
-                    : "memory");
-            }
+        bool fatal = false;
+        if (!dom_stage(d, cb, K, G.obj_bytes, obj, rs, cnt, bar, s_skip, parity, fatal)) {
+            if (fatal) break;
+            continue;
         }
-        for (int i = tid; i < kColBlock; i += blockDim.x) cnt[i] = 0;
-        __syncthreads();
-        if (*s_skip) continue;
-        if (!mbar_wait(bar, parity, kCopyWaitCycles)) {
-            if (tid == 0) set_status(d.sc, EMO_ERR_TIMEOUT);
-            mbar_wait(bar, parity, kCopyWaitCycles);
-            break;
-        }
-        parity ^= 1u;
-
         const int64_t n2 = d.in.n2;
         const int rbmax = min(d.nrb, 32 * (cb + 1));
         const int rb_lo = chunk * kDomRowChunk, rb_hi = min(rbmax, rb_lo + kDomRowChunk);
@@ -394,10 +408,8 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
         VCount<kDomNH> vc;
         for (int rb = rb_lo + warp; rb < rb_hi; rb += NW) {
             const int64_t pl = (int64_t)rb * kTileRows + lane;
-            for (int k = 0; k < K; ++k) {
-                const float* sv = reinterpret_cast<const float*>(obj + k * G.obj_bytes);
-                myst[k * 32 + lane] = pl < n2 ? count_ge(sv, __ldg(&d.keys[pl * K + k])) : 0;
-            }
+            for (int k = 0; k < K; ++k)
+                myst[k * 32 + lane] = pl < n2 ? count_ge_halves(obj + k * G.obj_bytes, __ldg(&d.keys[pl * K + k])) : 0;
             __syncwarp();
             const bool diag = (int64_t)rb * kTileRows + 31 >= cbase;
             const bool dup = rb * kTileRows + 31 >= dupcut;
@@ -412,14 +424,17 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
 #pragma unroll 1
                     for (int k = 0; k < K; ++k) {
                         const unsigned char* ob = obj + k * G.obj_bytes;
-                        const int tk = myst[k * 32 + i];
-                        const int c = tk >> G.log_cps;
+                        const int t = (myst[k * 32 + i] >> (16 * half)) & 0xFFFF;
+                        const int c = t >> G.log_cps;
                         uint32_t wk = reinterpret_cast<const uint32_t*>(ob + kPrefPbOff)[c * 32 + lane];
-                        const int rem = tk & (G.cps - 1);
-                        const uint16_t* so = reinterpret_cast<const uint16_t*>(ob + kPrefOrdOff) + (c << G.log_cps);
-                        for (int e = 0; e < rem; ++e) {
-                            const int col = so[e];
-                            if ((col >> 5) == lane) wk |= 1u << (col & 31);
+                        const int rem = t & (G.cps - 1);
+                        const uint16_t* so =
+                            reinterpret_cast<const uint16_t*>(ob + kPrefOrdOff) + half * kHalf + (c << G.log_cps);
+                        for (int e = 0; e < G.cps - 1; ++e) {
+                            if (e < rem) {
+                                const int col = so[e];
+                                if ((col >> 5) == lane) wk |= 1u << (col & 31);
+                            }
                         }
                         word &= wk;
                     }
@@ -442,13 +457,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
             }
             __syncwarp();
         }
-        flush_counts(vc, cnt, lane);
-        __syncthreads();
-        for (int q = tid; q < kColBlock; q += blockDim.x) {
-            const int c = cnt[(q & 31) * 32 + (q >> 5)];
-            if (c) atomicAdd(&d.cnt[cbase + q], c);
-        }
-        __syncthreads();
+        dom_flush_item(d, cbase, vc, cnt, lane);
     }
 }
 
