@@ -8,8 +8,8 @@
 //     (32 rows x 32 uint32 words).  Row block rb = rows [32 rb, 32 rb + 32),
 //     column block cb = columns [1024 cb, 1024 cb + 1024); tile (rb, cb)
 //     exists for cb >= rb / 32.  Tiles of a row block are contiguous; inside
-//     a tile, word w of row r sits at position r * 32 + (w ^ r) (an XOR
-//     swizzle that makes the row-per-lane shared-memory writes conflict free);
+//     a tile, word w of row r (columns 32 w .. 32 w + 31 of the block, bit b
+//     = column 32 w + b) sits at position r * 32 + w;
 //   * the objective keys used by the dominance kernel are the objectives
 //     2..m of each point in sorted order, array-of-structs with stride m-1,
 //     padded to a multiple of 1024 points with -inf;

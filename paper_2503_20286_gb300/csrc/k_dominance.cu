@@ -11,21 +11,23 @@
 //     a checkpoint bitset plus at most CPS - 1 extra bits (CPS = 1 for m <= 4,
 //     so no extra bits at all).
 //   k_dom_pref<M> (m <= 6; k_dom_pref_rt for m >= 7) -- one warp per row
-//     block, lane = word of the 32-word row segment of a column block (lanes
-//     0-15 in half 0, 16-31 in half 1): each lane first counts, for its row
-//     and each objective, the columns of both halves that are >= (binary
-//     search); then, row by row, the word is the AND over the objectives of
-//     the prefix bitsets, masked by q > p (diagonal blocks) and by the runs of
-//     identical points. Rows are stored as coalesced 128-byte segments of the
-//     tile; the dominator count of every column (column sums of D) is
-//     accumulated by a Harley-Seal bit-sliced counter per lane.
+//     block: each lane first counts, for its row and each objective, the
+//     columns of both halves that are >= (binary search). Then each half-warp
+//     builds one row at a time (lanes 0-15 rows 0-15, lanes 16-31 rows 16-31),
+//     a lane owning 64 columns (two words): the words are the AND over the
+//     objectives of the prefix bitsets, masked by q > p (diagonal blocks) and
+//     by the runs of identical points. One 64-bit store per lane writes two
+//     rows' 128-byte segments per warp instruction; the dominator count of
+//     every column (column sums of D) is accumulated by Harley-Seal
+//     bit-sliced counters per lane.
 // emo_dominance (caller order, full matrix): k_dom_full compares every
 //   ordered pair directly ("all <= and some <").
 #include "emo_kernels.cuh"
 
 namespace emo {
 
-constexpr int kDomNH = 8;  // high count planes: up to 4095 rows per lane and item
+constexpr int kDomNH = 5;  // high count planes: up to 511 rows per lane and item
+static_assert(kDomRowChunk / 16 * 16 < (1 << (4 + kDomNH)), "column counter overflow");
 constexpr long long kCopyWaitCycles = 1ll << 32;
 constexpr int kHalf = kColBlock / 2;
 
@@ -60,18 +62,26 @@ __device__ __forceinline__ void dom_decode(long long local, int ncb, int nrb, in
     chunk = (int)local;
 }
 
-// Flush a warp's per-lane column counters: lane w holds columns 32 w + b.
+// Flush a warp's per-lane column counters into s_cnt (column q of the block
+// at index (q % 32) * 32 + q / 32, conflict free for the warp): lane l and
+// lane l + 16 both count columns 64 (l % 16) .. + 63 over their own rows.
 template <int NH>
-__device__ __forceinline__ void flush_counts(VCount<NH>& vc, int32_t* s_cnt, int lane)
+__device__ __forceinline__ void flush_counts(VCount<NH>& vlo, VCount<NH>& vhi, int32_t* s_cnt, int lane)
 {
-    if (__any_sync(0xffffffffu, vc.any())) {
-#pragma unroll 4
+    if (__any_sync(0xffffffffu, vlo.any() || vhi.any())) {
+        const int w = 2 * (lane & 15) + (lane >> 4);  // word whose columns this lane flushes
+#pragma unroll 2
         for (int b = 0; b < 32; ++b) {
-            int c = vc.count(b);
-            if (c) atomicAdd(&s_cnt[b * 32 + lane], c);
+            int c = vlo.count(b);
+            c += __shfl_down_sync(0xffffffffu, c, 16);
+            int e = vhi.count(b);
+            e += __shfl_up_sync(0xffffffffu, e, 16);
+            const int v = lane < 16 ? c : e;
+            if (v) atomicAdd(&s_cnt[b * 32 + w], v);
         }
     }
-    vc = VCount<NH>();
+    vlo = VCount<NH>();
+    vhi = VCount<NH>();
 }
 
 // ------------------------------------------------------------ k_colprep
@@ -178,65 +188,78 @@ __device__ __forceinline__ int count_ge_halves(const unsigned char* ob, float x)
     return count_ge512(sv, x) | (count_ge512(sv + kHalf, x) << 16);
 }
 
-// Word of objective k's prefix set for the lane (packed half counts t01).
+// Two words (columns 64 l .. 64 l + 63, l = lane % 16) of an objective's
+// prefix set for a count t of the lane's half.
 template <int LOG_CPS>
-__device__ __forceinline__ uint32_t prefix_word(const unsigned char* ob, int t01, int lane)
+__device__ __forceinline__ unsigned long long prefix_word(const unsigned char* ob, int t, int l)
 {
-    const int half = lane >> 4;
-    const int t = (t01 >> (16 * half)) & 0xFFFF;
     const int c = t >> LOG_CPS;
-    uint32_t w = reinterpret_cast<const uint32_t*>(ob + kPrefPbOff)[c * 32 + lane];
+    unsigned long long w = *reinterpret_cast<const unsigned long long*>(ob + kPrefPbOff + c * 128 + l * 8);
     if (LOG_CPS > 0) {
         constexpr int CPS = 1 << LOG_CPS;
         const int rem = t & (CPS - 1);
-        const uint16_t* so = reinterpret_cast<const uint16_t*>(ob + kPrefOrdOff) + half * kHalf;
+        const uint16_t* so = reinterpret_cast<const uint16_t*>(ob + kPrefOrdOff) + (l >> 3) * kHalf;
 #pragma unroll
         for (int e = 0; e < CPS - 1; ++e) {
             const int col = so[min((c << LOG_CPS) + e, kHalf - 1)];
-            const bool hit = (e < rem) & ((col >> 5) == lane);
-            w |= hit ? (1u << (col & 31)) : 0u;
+            const bool hit = (e < rem) & ((col >> 6) == l);
+            w |= hit ? (1ull << (col & 63)) : 0ull;
         }
     }
     return w;
 }
 
-// Words of the 32 rows of row block rb in column block cb (lane = word).
+// Keep columns q > p of the lane's 64 (diagonal blocks), drop identical points.
+template <bool DIAG, bool DUP>
+__device__ __forceinline__ unsigned long long row_masks(unsigned long long word, int64_t prow, int64_t cbase,
+                                                        const int32_t* __restrict__ rs, int l)
+{
+    if (DIAG) {
+        const int64_t off = prow - (cbase + 64 * l);
+        const int sh = (int)(off < 0 ? 0 : (off > 62 ? 63 : off + 1));  // shift count in [0, 63]
+        word &= off >= 63 ? 0ull : (off >= 0 ? ~0ull << sh : ~0ull);
+    }
+    if (DUP && word) {
+#pragma unroll 4
+        for (int bb = 0; bb < 64; ++bb) {
+            const int b = (bb + l) & 63;
+            if ((int64_t)rs[64 * l + b] <= prow) word &= ~(1ull << b);
+        }
+    }
+    return word;
+}
+
+// The 32 rows of row block rb in column block cb; t[k] is the packed count
+// (half 0 | half 1 << 16) of objective k for the lane's row.
 // DIAG: the row block overlaps the column block (keep q > p only).
 // DUP: a run of identical points may reach into the column block.
 template <int K, bool DIAG, bool DUP>
 __device__ __forceinline__ void pref_rows(const unsigned char* __restrict__ obj, const int32_t* __restrict__ rs,
                                           const int (&t)[K], int64_t rowbase, int64_t cbase, uint32_t* tile,
-                                          VCount<kDomNH>& vc, int lane)
+                                          VCount<kDomNH>& vlo, VCount<kDomNH>& vhi, int lane)
 {
     using S = PrefShape<K>;
+    const int l = lane & 15, h = lane >> 4, hs = (l >> 3) * 16;
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(tile + h * 16 * 32) + l;
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        uint32_t x[16];
+    for (int g = 0; g < 2; ++g) {
+        uint32_t xl[8], xh[8];
 #pragma unroll
-        for (int ii = 0; ii < 16; ++ii) {
-            const int i = h * 16 + ii;
-            uint32_t word = 0xFFFFFFFFu;
+        for (int jj = 0; jj < 8; ++jj) {
+            const int j = g * 8 + jj, i = j + 16 * h;
+            unsigned long long word = ~0ull;
 #pragma unroll
-            for (int k = 0; k < K; ++k)
-                word &= prefix_word<S::LOG_CPS>(obj + k * S::OBJ_BYTES, __shfl_sync(0xffffffffu, t[k], i), lane);
-            const int64_t prow = rowbase + i;
-            if (DIAG) {
-                const int64_t off = prow - (cbase + 32 * lane);  // keep columns q > p
-                const int sh = (int)(off < 0 ? 0 : (off > 30 ? 31 : off + 1));  // shift count in [0, 31]
-                word &= off >= 31 ? 0u : (off >= 0 ? 0xFFFFFFFFu << sh : 0xFFFFFFFFu);
+            for (int k = 0; k < K; ++k) {
+                const int tk = (__shfl_sync(0xffffffffu, t[k], i) >> hs) & 0xFFFF;
+                word &= prefix_word<S::LOG_CPS>(obj + k * S::OBJ_BYTES, tk, l);
             }
-            if (DUP) {
-                // identical points (same run) never dominate each other
-#pragma unroll 4
-                for (int bb = 0; bb < 32; ++bb) {
-                    const int b = (bb + lane) & 31;
-                    if ((int64_t)rs[32 * lane + b] <= prow) word &= ~(1u << b);
-                }
-            }
-            __stcs(&tile[i * 32 + (lane ^ i)], word);
-            x[ii] = word;
+            word = row_masks<DIAG, DUP>(word, rowbase + i, cbase, rs, l);
+            __stcs(dst + j * 16, word);
+            xl[jj] = (uint32_t)word;
+            xh[jj] = (uint32_t)(word >> 32);
         }
-        vc.add16(x);
+        vlo.add8(xl);
+        vhi.add8(xh);
     }
 }
 
@@ -284,10 +307,10 @@ __device__ __forceinline__ bool dom_stage(const ProbDev& d, int cb, int K, int o
 }
 
 // Column counts of the item: smem reduction, one global atomic per column.
-__device__ __forceinline__ void dom_flush_item(const ProbDev& d, int64_t cbase, VCount<kDomNH>& vc, int32_t* cnt,
-                                               int lane)
+__device__ __forceinline__ void dom_flush_item(const ProbDev& d, int64_t cbase, VCount<kDomNH>& vlo,
+                                               VCount<kDomNH>& vhi, int32_t* cnt, int lane)
 {
-    flush_counts(vc, cnt, lane);
+    flush_counts(vlo, vhi, cnt, lane);
     __syncthreads();
     for (int q = threadIdx.x; q < kColBlock; q += blockDim.x) {
         const int c = cnt[(q & 31) * 32 + (q >> 5)];
@@ -329,7 +352,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
         const int rb_lo = chunk * kDomRowChunk, rb_hi = min(rbmax, rb_lo + kDomRowChunk);
         const int dupcut = d.minrs[cb];
         const int64_t cbase = (int64_t)cb * kColBlock;
-        VCount<kDomNH> vc;
+        VCount<kDomNH> vlo, vhi;
 
         // keys of the lane's row in the warp's next row block (prefetched)
         float key[K];
@@ -353,11 +376,11 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
             const bool dup = rb * kTileRows + 31 >= dupcut;
             const int64_t rowbase = (int64_t)rb * kTileRows;
             uint32_t* tile = d.D + tile_index(rb, cb, d.ncb) * (int64_t)(kTileRows * kTileWords);
-            if (dup) pref_rows<K, true, true>(sm.obj, sm.rs, t, rowbase, cbase, tile, vc, lane);
-            else if (diag) pref_rows<K, true, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vc, lane);
-            else pref_rows<K, false, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vc, lane);
+            if (dup) pref_rows<K, true, true>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
+            else if (diag) pref_rows<K, true, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
+            else pref_rows<K, false, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
         }
-        dom_flush_item(d, cbase, vc, sm.cnt, lane);
+        dom_flush_item(d, cbase, vlo, vhi, sm.cnt, lane);
     }
 }
 
@@ -380,7 +403,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
     int* s_skip = reinterpret_cast<int*>(s_item + 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int32_t* myst = st + warp * K * 32;
-    const int half = lane >> 4;
+    const int l = lane & 15, h = lane >> 4, half = l >> 3, hs = half * 16;
     if (tid == 0) mbar_init(bar, 1);
     __syncthreads();
     uint32_t parity = 0;
@@ -405,7 +428,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
         const int rb_lo = chunk * kDomRowChunk, rb_hi = min(rbmax, rb_lo + kDomRowChunk);
         const int dupcut = d.minrs[cb];
         const int64_t cbase = (int64_t)cb * kColBlock;
-        VCount<kDomNH> vc;
+        VCount<kDomNH> vlo, vhi;
         for (int rb = rb_lo + warp; rb < rb_hi; rb += NW) {
             const int64_t pl = (int64_t)rb * kTileRows + lane;
             for (int k = 0; k < K; ++k)
@@ -414,54 +437,48 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
             const bool diag = (int64_t)rb * kTileRows + 31 >= cbase;
             const bool dup = rb * kTileRows + 31 >= dupcut;
             uint32_t* tile = d.D + tile_index(rb, cb, d.ncb) * (int64_t)(kTileRows * kTileWords);
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(tile + h * 16 * 32) + l;
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                uint32_t x[16];
+            for (int g = 0; g < 2; ++g) {
+                uint32_t xl[8], xh[8];
 #pragma unroll
-                for (int ii = 0; ii < 16; ++ii) {
-                    const int i = h * 16 + ii;
-                    uint32_t word = 0xFFFFFFFFu;
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = g * 8 + jj, i = j + 16 * h;
+                    unsigned long long word = ~0ull;
 #pragma unroll 1
                     for (int k = 0; k < K; ++k) {
                         const unsigned char* ob = obj + k * G.obj_bytes;
-                        const int t = (myst[k * 32 + i] >> (16 * half)) & 0xFFFF;
+                        const int t = (myst[k * 32 + i] >> hs) & 0xFFFF;
                         const int c = t >> G.log_cps;
-                        uint32_t wk = reinterpret_cast<const uint32_t*>(ob + kPrefPbOff)[c * 32 + lane];
+                        unsigned long long wk =
+                            *reinterpret_cast<const unsigned long long*>(ob + kPrefPbOff + c * 128 + l * 8);
                         const int rem = t & (G.cps - 1);
                         const uint16_t* so =
                             reinterpret_cast<const uint16_t*>(ob + kPrefOrdOff) + half * kHalf + (c << G.log_cps);
-                        for (int e = 0; e < G.cps - 1; ++e) {
-                            if (e < rem) {
-                                const int col = so[e];
-                                if ((col >> 5) == lane) wk |= 1u << (col & 31);
-                            }
+                        for (int e = 0; e < rem; ++e) {
+                            const int col = so[e];
+                            if ((col >> 6) == l) wk |= 1ull << (col & 63);
                         }
                         word &= wk;
                     }
                     const int64_t prow = (int64_t)rb * kTileRows + i;
-                    if (diag) {
-                        const int64_t off = prow - (cbase + 32 * lane);
-                        if (off >= 31) word = 0u;
-                        else if (off >= 0) word &= 0xFFFFFFFFu << (int)(off + 1);
-                    }
-                    if (dup && word) {
-                        for (int bb = 0; bb < 32; ++bb) {
-                            const int b = (bb + lane) & 31;
-                            if ((int64_t)rs[32 * lane + b] <= prow) word &= ~(1u << b);
-                        }
-                    }
-                    __stcs(&tile[i * 32 + (lane ^ i)], word);
-                    x[ii] = word;
+                    if (dup) word = row_masks<true, true>(word, prow, cbase, rs, l);
+                    else if (diag) word = row_masks<true, false>(word, prow, cbase, rs, l);
+                    __stcs(dst + j * 16, word);
+                    xl[jj] = (uint32_t)word;
+                    xh[jj] = (uint32_t)(word >> 32);
                 }
-                vc.add16(x);
+                vlo.add8(xl);
+                vhi.add8(xh);
             }
             __syncwarp();
         }
-        dom_flush_item(d, cbase, vc, cnt, lane);
+        dom_flush_item(d, cbase, vlo, vhi, cnt, lane);
     }
 }
 
 // Full matrix in caller order: D_ij = all(F_i <= F_j) and any(F_i < F_j).
+constexpr int kFullNH = 8;  // up to 4095 rows per lane and item
 template <int M>
 struct FullSmem {
     alignas(16) float ck[kColBlock * M];
@@ -490,7 +507,7 @@ __global__ void __launch_bounds__(256, 1) k_dom_full(const float* __restrict__ F
         for (int i = tid; i < kColBlock; i += blockDim.x) sm.cnt[i] = 0;
         __syncthreads();
         const int rb_lo = chunk * kDomRowChunk, rb_hi = min(nrb, rb_lo + kDomRowChunk);
-        VCount<kDomNH> vc;
+        VCount<kFullNH> vc;
         for (int rbg = rb_lo + warp * R; rbg < rb_hi; rbg += NW * R) {
             float rk[R][M];
             int64_t prow[R];
@@ -545,7 +562,13 @@ __global__ void __launch_bounds__(256, 1) k_dom_full(const float* __restrict__ F
             __syncwarp();
         }
         if (cnt) {
-            flush_counts(vc, sm.cnt, lane);
+            if (__any_sync(0xffffffffu, vc.any())) {
+#pragma unroll 4
+                for (int b = 0; b < 32; ++b) {
+                    const int c = vc.count(b);
+                    if (c) atomicAdd(&sm.cnt[b * 32 + lane], c);
+                }
+            }
             __syncthreads();
             for (int q = tid; q < kColBlock; q += blockDim.x) {
                 const int c = sm.cnt[(q & 31) * 32 + (q >> 5)];

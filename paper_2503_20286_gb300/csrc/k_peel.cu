@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                             const uint32_t e = (uint32_t)s_mem[i];
                             const uint32_t r = e & 31u;
                             const int64_t t = (int64_t)(e >> 5) + cb;
-                            x[j] = __ldcs(&d.D[(t << 10) + (r << 5) + (lane ^ r)]);
+                            x[j] = __ldcs(&d.D[(t << 10) + (r << 5) + lane]);
                         }
                     }
                 };
