@@ -166,20 +166,30 @@ __host__ __device__ __forceinline__ int64_t tile_index(int64_t rb, int64_t cb, i
 }
 
 // Column-block prefix sets of the dominance kernel. Each 1024-column block
-// is split into two halves of 512 columns. For each half and key objective k
-// (objectives 2..m): the half's columns sorted by f_k descending (values and
-// local indices), and the bitsets of the first c * cps sorted columns of the
-// half for c = 0..512/cps. The bitsets of both halves are interleaved: row c
-// holds 32 words, words 0-15 from half 0 and 16-31 from half 1, so the word w
-// of a tile row always comes from half w / 16.
-//   per objective: float sv[2][512] | uint16 ord[2][512] | uint32 pb[512/cps + 1][32]
+// is split into two halves of 512 columns. For each key objective k
+// (objectives 2..m) the block stores:
+//   fv   -- the block's 1024 values of f_k sorted descending;
+//   cum0 -- cum0[j] = how many of the first j entries of fv lie in half 0
+//           (so a count j of values >= x splits into cum0[j] and j - cum0[j]);
+//   pb   -- for each half, the bitsets of its first c * cps columns in the
+//           order of f_k descending, c = 0..512/cps. Row c holds 32 words,
+//           words 0-15 from half 0 and 16-31 from half 1, so the word w of a
+//           tile row always comes from half w / 16;
+//   ord  -- (cps > 1 only) each half's local column indices in that order.
+//   per objective: float fv[1024] | uint16 cum0[1025] (+pad) | uint32 pb[512/cps + 1][32] | uint16 ord[2][512]
+constexpr int kPrefCumOff = kColBlock * 4;
+constexpr int kPrefPbOff = kPrefCumOff + 2176;  // 1025 uint16 rounded up to 128 bytes
 __host__ __device__ constexpr int colprep_log_cps(int K)
 {
     return K <= 3 ? 0 : (K <= 5 ? 1 : (K <= 6 ? 2 : (K <= 9 ? 3 : 4)));
 }
+__host__ __device__ constexpr int64_t colprep_ord_off(int K)
+{
+    return kPrefPbOff + (((kColBlock / 2) >> colprep_log_cps(K)) + 1) * 32 * 4;
+}
 __host__ __device__ constexpr int64_t colprep_obj_bytes(int K)
 {
-    return kColBlock * 4 + kColBlock * 2 + (((kColBlock / 2) >> colprep_log_cps(K)) + 1) * 32 * 4;
+    return colprep_ord_off(K) + (colprep_log_cps(K) > 0 ? kColBlock * 2 : 0);
 }
 
 // Byte layout of one problem region; fills `d` when base != 0. Returns the
@@ -273,11 +283,18 @@ __host__ __device__ __forceinline__ int64_t dom_items_of_cb(int64_t cb, int64_t 
     int64_t rbs = nrb < 32 * (cb + 1) ? nrb : 32 * (cb + 1);
     return cdiv(rbs, kDomRowChunk);
 }
+// Items of column blocks 0 .. c-1 in closed form: block cb < nrb / 32 has
+// cb / 8 + 1 items (its 32 (cb + 1) row blocks in chunks of 256), every later
+// block has cdiv(nrb, 256).
+static_assert(kDomRowChunk == 256, "dom_items_prefix assumes 8 column blocks of rows per chunk");
+__host__ __device__ __forceinline__ int64_t dom_items_prefix(int64_t c, int64_t nrb)
+{
+    const int64_t A = nrb / 32, a = c < A ? c : A, q = a >> 3, r = a & 7;
+    return (q + 1) * (4 * q + r) + (c > A ? (c - A) * cdiv(nrb, kDomRowChunk) : 0);
+}
 __host__ __device__ inline int64_t dom_items_of(int64_t n2)
 {
-    int64_t nrb = cdiv(n2, 32), ncb = cdiv(n2, kColBlock), s = 0;
-    for (int64_t cb = 0; cb < ncb; ++cb) s += dom_items_of_cb(cb, nrb);
-    return s;
+    return dom_items_prefix(cdiv(n2, kColBlock), cdiv(n2, 32));
 }
 
 constexpr int kAscPointsPerItem = 2048;

@@ -33,33 +33,36 @@ constexpr int kHalf = kColBlock / 2;
 
 // Geometry of the per-objective prefix-set blocks (runtime form).
 struct PrefGeom {
-    int log_cps, cps, obj_bytes;
+    int log_cps, cps, obj_bytes, ord_off;
     __device__ __forceinline__ explicit PrefGeom(int K)
-        : log_cps(colprep_log_cps(K)), cps(1 << colprep_log_cps(K)), obj_bytes((int)colprep_obj_bytes(K))
+        : log_cps(colprep_log_cps(K)), cps(1 << colprep_log_cps(K)), obj_bytes((int)colprep_obj_bytes(K)),
+          ord_off((int)colprep_ord_off(K))
     {
     }
 };
-constexpr int kPrefOrdOff = kColBlock * 4;  // offsets inside one objective block
-constexpr int kPrefPbOff = kColBlock * 6;
 
 template <int K>
 struct PrefShape {
     static constexpr int LOG_CPS = colprep_log_cps(K);
     static constexpr int CPS = 1 << LOG_CPS;
     static constexpr int OBJ_BYTES = (int)colprep_obj_bytes(K);
+    static constexpr int ORD_OFF = (int)colprep_ord_off(K);
 };
 
 // Decode a dominance item of one problem: column blocks are served from the
 // last (tallest) to the first; each is split into chunks of kDomRowChunk row
-// blocks.
+// blocks. Binary search over the closed-form item prefix.
 __device__ __forceinline__ void dom_decode(long long local, int ncb, int nrb, int& cb, int& chunk)
 {
-    for (cb = ncb - 1; cb >= 0; --cb) {
-        long long n = dom_items_of_cb(cb, nrb);
-        if (local < n) break;
-        local -= n;
+    const long long u = dom_items_prefix(ncb, nrb) - local;  // in 1 .. total
+    int lo = 1, hi = ncb;                                     // smallest c with prefix(c) >= u
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (dom_items_prefix(mid, nrb) >= u) hi = mid;
+        else lo = mid + 1;
     }
-    chunk = (int)local;
+    cb = lo - 1;
+    chunk = (int)(dom_items_prefix(lo, nrb) - u);
 }
 
 // Flush a warp's per-lane column counters into s_cnt (column q of the block
@@ -68,13 +71,14 @@ __device__ __forceinline__ void dom_decode(long long local, int ncb, int nrb, in
 template <int NH>
 __device__ __forceinline__ void flush_counts(VCount<NH>& vlo, VCount<NH>& vhi, int32_t* s_cnt, int lane)
 {
-    if (__any_sync(0xffffffffu, vlo.any() || vhi.any())) {
+    const int top = max(vlo.top_plane(), vhi.top_plane());  // planes above are zero in every lane
+    if (top >= 0) {
         const int w = 2 * (lane & 15) + (lane >> 4);  // word whose columns this lane flushes
 #pragma unroll 2
         for (int b = 0; b < 32; ++b) {
-            int c = vlo.count(b);
+            int c = vlo.count_upto(b, top);
             c += __shfl_down_sync(0xffffffffu, c, 16);
-            int e = vhi.count(b);
+            int e = vhi.count_upto(b, top);
             e += __shfl_up_sync(0xffffffffu, e, 16);
             const int v = lane < 16 ? c : e;
             if (v) atomicAdd(&s_cnt[b * 32 + w], v);
@@ -85,11 +89,28 @@ __device__ __forceinline__ void flush_counts(VCount<NH>& vlo, VCount<NH>& vhi, i
 }
 
 // ------------------------------------------------------------ k_colprep
+// Entries of a descending array of 512 floats that are >= x (strict: > x).
+template <bool STRICT>
+__device__ __forceinline__ int count_before512(const float* v, float x)
+{
+    int pos = 0;
+#pragma unroll
+    for (int step = 256; step > 0; step >>= 1) {
+        const float y = v[pos + step - 1];
+        if (STRICT ? y > x : y >= x) pos += step;
+    }
+    const float y = v[pos];
+    if (STRICT ? y > x : y >= x) ++pos;
+    return pos;
+}
+
 __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int plast)
 {
     __shared__ float s_v[kColBlock];
     __shared__ uint16_t s_i[kColBlock];
+    __shared__ uint8_t s_mark[kColBlock];
     __shared__ uint32_t s_part[8][32];
+    __shared__ int s_warp[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int p = pfirst; p < plast; ++p) {
         const ProbDev& d = plan->p[p];
@@ -125,12 +146,21 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
                     __syncthreads();
                 }
             }
-            float* sv = reinterpret_cast<float*>(blk);
-            uint16_t* so = reinterpret_cast<uint16_t*>(blk + kPrefOrdOff);
+            float* fv = reinterpret_cast<float*>(blk);
+            uint16_t* cum0 = reinterpret_cast<uint16_t*>(blk + kPrefCumOff);
             uint32_t* pb = reinterpret_cast<uint32_t*>(blk + kPrefPbOff);
+            if (G.log_cps > 0) {
+                uint16_t* so = reinterpret_cast<uint16_t*>(blk + G.ord_off);
+                for (int q = tid; q < kColBlock; q += blockDim.x) so[q] = s_i[q];
+            }
+            // merge of the halves into the full descending order (ties: half 0
+            // first); mark the half-0 positions
             for (int q = tid; q < kColBlock; q += blockDim.x) {
-                sv[q] = s_v[q];
-                so[q] = s_i[q];
+                const float x = s_v[q];
+                const int rank = (q & (kHalf - 1)) +
+                                 (q < kHalf ? count_before512<true>(s_v + kHalf, x) : count_before512<false>(s_v, x));
+                fv[rank] = x;
+                s_mark[rank] = q < kHalf;
             }
             // interleaved prefix bitsets: lane w builds word w from the sorted
             // columns of half w / 16; warp v covers checkpoints (v*seg, (v+1)*seg]
@@ -154,6 +184,18 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
                 }
                 pb[(c + 1) * 32 + lane] = acc;
             }
+            // cum0[j] = half-0 entries among the first j of the full order
+            {
+                const int j0 = tid * 4;  // 256 threads x 4 entries
+                const int m0 = s_mark[j0], m1 = s_mark[j0 + 1], m2 = s_mark[j0 + 2], m3 = s_mark[j0 + 3];
+                int tot;
+                const int ex = block_exclusive_scan<256>(m0 + m1 + m2 + m3, s_warp, tot);
+                if (tid == 0) cum0[0] = 0;
+                cum0[j0 + 1] = (uint16_t)(ex + m0);
+                cum0[j0 + 2] = (uint16_t)(ex + m0 + m1);
+                cum0[j0 + 3] = (uint16_t)(ex + m0 + m1 + m2);
+                cum0[j0 + 4] = (uint16_t)(ex + m0 + m1 + m2 + m3);
+            }
             __syncthreads();
         }
     }
@@ -170,27 +212,24 @@ struct PrefSmem {
     int skip;
 };
 
-// Number of entries >= x in a descending array of 512 floats.
-__device__ __forceinline__ int count_ge512(const float* sv, float x)
-{
-    int pos = 0;
-#pragma unroll
-    for (int step = 256; step > 0; step >>= 1)
-        if (sv[pos + step - 1] >= x) pos += step;
-    if (sv[pos] >= x) ++pos;
-    return pos;
-}
-
-// Packed counts of both halves of one objective: t0 | t1 << 16.
+// Packed counts of the block's values >= x in both halves of one objective:
+// t0 | t1 << 16 (binary search over the full descending order, then the
+// half-0 share of that prefix).
 __device__ __forceinline__ int count_ge_halves(const unsigned char* ob, float x)
 {
-    const float* sv = reinterpret_cast<const float*>(ob);
-    return count_ge512(sv, x) | (count_ge512(sv + kHalf, x) << 16);
+    const float* fv = reinterpret_cast<const float*>(ob);
+    int pos = 0;
+#pragma unroll
+    for (int step = kColBlock / 2; step > 0; step >>= 1)
+        if (fv[pos + step - 1] >= x) pos += step;
+    if (fv[pos] >= x) ++pos;
+    const int t0 = reinterpret_cast<const uint16_t*>(ob + kPrefCumOff)[pos];
+    return t0 | ((pos - t0) << 16);
 }
 
 // Two words (columns 64 l .. 64 l + 63, l = lane % 16) of an objective's
 // prefix set for a count t of the lane's half.
-template <int LOG_CPS>
+template <int LOG_CPS, int ORD_OFF>
 __device__ __forceinline__ unsigned long long prefix_word(const unsigned char* ob, int t, int l)
 {
     const int c = t >> LOG_CPS;
@@ -198,7 +237,7 @@ __device__ __forceinline__ unsigned long long prefix_word(const unsigned char* o
     if (LOG_CPS > 0) {
         constexpr int CPS = 1 << LOG_CPS;
         const int rem = t & (CPS - 1);
-        const uint16_t* so = reinterpret_cast<const uint16_t*>(ob + kPrefOrdOff) + (l >> 3) * kHalf;
+        const uint16_t* so = reinterpret_cast<const uint16_t*>(ob + ORD_OFF) + (l >> 3) * kHalf;
 #pragma unroll
         for (int e = 0; e < CPS - 1; ++e) {
             const int col = so[min((c << LOG_CPS) + e, kHalf - 1)];
@@ -251,7 +290,7 @@ __device__ __forceinline__ void pref_rows(const unsigned char* __restrict__ obj,
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int tk = (__shfl_sync(0xffffffffu, t[k], i) >> hs) & 0xFFFF;
-                word &= prefix_word<S::LOG_CPS>(obj + k * S::OBJ_BYTES, tk, l);
+                word &= prefix_word<S::LOG_CPS, S::ORD_OFF>(obj + k * S::OBJ_BYTES, tk, l);
             }
             word = row_masks<DIAG, DUP>(word, rowbase + i, cbase, rs, l);
             __stcs(dst + j * 16, word);
@@ -454,7 +493,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
                             *reinterpret_cast<const unsigned long long*>(ob + kPrefPbOff + c * 128 + l * 8);
                         const int rem = t & (G.cps - 1);
                         const uint16_t* so =
-                            reinterpret_cast<const uint16_t*>(ob + kPrefOrdOff) + half * kHalf + (c << G.log_cps);
+                            reinterpret_cast<const uint16_t*>(ob + G.ord_off) + half * kHalf + (c << G.log_cps);
                         for (int e = 0; e < rem; ++e) {
                             const int col = so[e];
                             if ((col >> 6) == l) wk |= 1ull << (col & 63);

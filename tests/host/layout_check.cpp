@@ -16,7 +16,7 @@ static int fail(const char* what, long long a, long long b)
 
 int main()
 {
-    const long long sizes[] = {1, 31, 32, 33, 1023, 1024, 1025, 4096, 5000, 33000, 400000};
+    const long long sizes[] = {1, 31, 32, 33, 1023, 1024, 1025, 4096, 5000, 8191, 8192, 8193, 33000, 262145, 400000};
     for (long long n2 : sizes) {
         const long long nrb = cdiv(n2, 32), ncb = cdiv(n2, kColBlock);
         // tiles are enumerated row block by row block, column blocks cb >= rb / 32
@@ -46,6 +46,12 @@ int main()
             }
         }
         if (items != dom_items_of(n2)) return fail("dom_items_of", items, dom_items_of(n2));
+        // closed-form item prefix against the per-block sum
+        long long pre = 0;
+        for (long long cb = 0; cb <= ncb; ++cb) {
+            if (dom_items_prefix(cb, nrb) != pre) return fail("dom_items_prefix", dom_items_prefix(cb, nrb), pre);
+            if (cb < ncb) pre += dom_items_of_cb(cb, nrb);
+        }
         for (long long t = 0; t < idx; ++t)
             if (seen[t] != 1) return fail("tile coverage", t, seen[t]);
         // workspace: regions are 256-byte aligned, disjoint and inside the size
