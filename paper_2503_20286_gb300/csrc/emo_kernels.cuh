@@ -182,9 +182,15 @@ __global__ void k_prep(Plan* plan);
 __global__ void k_sort(Plan* plan);
 __global__ void k_peel(Plan* plan);
 
-constexpr int kPeelChunk = 8192;   // front members staged in shared memory at once
-// Dynamic shared memory of k_peel for ncb column blocks.
-__host__ __device__ constexpr int peel_smem_bytes(int ncb) { return (ncb + 1 + kPeelChunk) * (int)sizeof(int); }
+constexpr int kPeelChunk = 4096;   // front members staged in shared memory at once
+constexpr int kPeelStages = 3;     // per-warp ring of 32-row copies in flight
+constexpr int kPeelRingBytes = (kCoopThreads / 32) * kPeelStages * 32 * 128;
+// Dynamic shared memory of k_peel for ncb column blocks: the copy ring, the
+// member prefix per block and the staged members.
+__host__ __device__ constexpr int peel_smem_bytes(int ncb)
+{
+    return kPeelRingBytes + (ncb + 1 + kPeelChunk) * (int)sizeof(int);
+}
 __global__ void k_stats(Plan* plan);
 __global__ void k_rescan(Plan* plan);
 __global__ void k_csr(Plan* plan);

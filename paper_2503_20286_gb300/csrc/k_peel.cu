@@ -3,29 +3,48 @@
 // with c the number of dominators of each point (column sums of D).
 //
 // One cooperative launch per call. Each CTA of a problem's group owns whole
-// column blocks (1024 sorted points) and their counts. Per front, the CTA
-// stages the members whose rows reach its blocks in shared memory, then for
-// every member reads the 128-byte segment of row p that falls in a block it
-// owns (one coalesced 4-byte load per lane; the next 16 members' loads are
-// in flight while the current 16 are counted) and adds the words into
-// per-lane Harley-Seal bit-sliced counters, giving d_j. Points whose count
-// reaches zero form the next front. One bounded group barrier separates
-// fronts. Selection stops once the fronts peeled hold n_keep points (that
-// front is l); ranking may continue to the end.
+// column blocks (1024 sorted points) and their counts; blocks are dealt in
+// descending order in a snake over the CTAs (block cb has about cb + 1 units
+// of work per front, so the snake keeps the largest CTA load within a few
+// blocks of the mean). Per front, the CTA stages the members whose rows reach
+// its blocks in shared memory; for each owned block every warp copies the
+// 128-byte row segments of 32 members at a time into its own ring of
+// shared-memory stages with cp.async (two batches in flight while the third
+// is counted), then adds the words into per-lane Harley-Seal bit-sliced
+// counters, giving d_j. Points whose count reaches zero form the next front.
+// One bounded group barrier separates fronts. Selection stops once the fronts
+// peeled hold n_keep points (that front is l); ranking may continue to the
+// end.
 #include "emo_kernels.cuh"
 
 namespace emo {
 
 constexpr int kPeelNH = 18;  // counter planes: 4 + 18 bits per column and warp
 
+// Column block dealt to CTA `rank` of a group of G in round r (snake order
+// over the blocks from the last to the first); -1 past the end.
+__device__ __forceinline__ int peel_block(int r, int rank, int G, int ncb)
+{
+    const int o = r * G + ((r & 1) ? G - 1 - rank : rank);
+    return o < ncb ? ncb - 1 - o : -1;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
 {
     constexpr int NW = kCoopThreads / 32;
     __shared__ int s_cnt[kColBlock];
-    __shared__ int s_newn;
+    __shared__ int s_newn, s_base;
     __shared__ int s_warp[33];
-    extern __shared__ int s_dyn[];  // [ncb + 1] member prefix per block, [kPeelChunk] staged members
-    int* s_pref = s_dyn;
+    // [ring] per-warp copy stages | [ncb + 1] member prefix per block | [kPeelChunk] staged members
+    extern __shared__ __align__(128) int s_dyn[];
 
     const Group g = group_of(plan);
     const ProbDev& d = plan->p[g.prob];
@@ -35,11 +54,15 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n2 = in.n2, n2p = d.n2p;
     const int ncb = d.ncb;
-    int* s_mem = s_dyn + ncb + 1;
+    uint32_t* ring = reinterpret_cast<uint32_t*>(s_dyn) + warp * (kPeelStages * 32 * 32);
+    int* s_pref = s_dyn + kPeelRingBytes / 4;
+    int* s_mem = s_pref + ncb + 1;
     const int64_t target = in.n_keep > 0 ? in.n_keep : n2;
 
     // ---- front 0: points without dominators
-    for (int cb = g.rank; cb < ncb; cb += g.size) {
+    for (int r = 0;; ++r) {
+        const int cb = peel_block(r, g.rank, g.size, ncb);
+        if (cb < 0) break;
         if (tid == 0) s_newn = 0;
         __syncthreads();
         for (int q = tid; q < kColBlock; q += blockDim.x) {
@@ -58,6 +81,8 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
     }
     if (!group_sync(d.sc, g.size, budget)) return;
 
+    // the largest owned block is the first one dealt
+    const int last_cb = peel_block(0, g.rank, g.size, ncb);
     int64_t prev_total = 0, total = ld_volatile(&d.sc->ranked);
     int k = 0;
     while (total < target) {
@@ -72,7 +97,6 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
         int32_t* fwn = d.front_n + (int64_t)nxt * ncb;
 
         // prefix of the member counts of every column block up to the last owned one
-        const int last_cb = g.rank < ncb ? g.rank + ((ncb - 1 - g.rank) / g.size) * g.size : -1;
         if (last_cb >= 0) {
             int run = 0;
             for (int base = 0; base <= last_cb; base += blockDim.x) {
@@ -107,45 +131,61 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                 s_mem[i] = (int)(base * 32u + (uint32_t)(p & 31));
             }
             __syncthreads();
-            for (int cb = g.rank; cb < ncb; cb += g.size) {
+            for (int r = 0;; ++r) {
+                const int cb = peel_block(r, g.rank, g.size, ncb);
+                if (cb < 0) break;
                 const int nmem = min(mc, s_pref[cb + 1] - m0);  // staged members reaching cb
                 if (nmem <= 0) continue;
                 for (int q = tid; q < kColBlock; q += blockDim.x) s_cnt[q] = 0;
-                if (tid == 0) s_newn = 0;
+                // new members of one block may arrive over several member chunks:
+                // append after those found in the earlier chunks of this front
+                if (tid == 0) s_base = s_newn = m0 == 0 ? 0 : fwn[cb];
                 __syncthreads();
                 VCount<kPeelNH> vc;
-                auto load16 = [&](int b0, uint32_t (&x)[16]) {
+                // copies of the warp's batches b = warp, warp + NW, ... (32 members each):
+                // lane copies 16 bytes (words 4 q .. 4 q + 3) of row j = 4 it + lane / 8
+                const int nb = (nmem + 31) >> 5;
+                auto issue = [&](int b, int stage) {
+                    uint32_t* dst = ring + stage * (32 * 32);
+                    const int q = lane & 7;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int i = b0 + j;
-                        x[j] = 0u;
-                        if (i < nmem) {
+                    for (int it = 0; it < 8; ++it) {
+                        const int j = it * 4 + (lane >> 3), i = b * 32 + j;
+                        if (b < nb && i < nmem) {
                             const uint32_t e = (uint32_t)s_mem[i];
-                            const uint32_t r = e & 31u;
                             const int64_t t = (int64_t)(e >> 5) + cb;
-                            x[j] = __ldcs(&d.D[(t << 10) + (r << 5) + lane]);
+                            cp_async16(smem_u32(dst + j * 32 + q * 4), d.D + (t << 10) + ((e & 31u) << 5) + q * 4);
                         }
                     }
+                    cp_async_commit();
                 };
-                uint32_t xa[16], xb[16];
-                int b0 = warp * 16;
-                if (b0 < nmem) load16(b0, xa);
-                while (b0 < nmem) {
-                    const int b1 = b0 + NW * 16;
-                    if (b1 < nmem) load16(b1, xb);  // next batch in flight while this one is counted
-                    vc.add16(xa);
-                    b0 = b1;
-                    if (b0 >= nmem) break;
-                    const int b2 = b0 + NW * 16;
-                    if (b2 < nmem) load16(b2, xa);
-                    vc.add16(xb);
-                    b0 = b2;
+                int b = warp, st = 0;
+                issue(b, 0);
+                issue(b + NW, 1);
+                for (; b < nb; b += NW) {
+                    issue(b + 2 * NW, (st + 2) % kPeelStages);
+                    cp_async_wait<2>();
+                    __syncwarp();
+                    const uint32_t* src = ring + st * (32 * 32);
+                    const int nrow = min(32, nmem - b * 32);
+                    uint32_t x[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) x[j] = j < nrow ? src[j * 32 + lane] : 0u;
+                    vc.add16(x);
+                    if (nrow > 16) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) x[j] = j + 16 < nrow ? src[(j + 16) * 32 + lane] : 0u;
+                        vc.add16(x);
+                    }
+                    __syncwarp();  // the stage is refilled two iterations later
+                    st = (st + 1) % kPeelStages;
                 }
+                cp_async_wait<0>();  // no copy outlives the block (the tail batches were empty)
                 const int top = vc.top_plane();
                 if (top >= 0) {
-                    for (int b = 0; b < 32; ++b) {
-                        const int c = vc.count_upto(b, top);
-                        if (c) atomicAdd(&s_cnt[b * 32 + lane], c);
+                    for (int bb = 0; bb < 32; ++bb) {
+                        const int c = vc.count_upto(bb, top);
+                        if (c) atomicAdd(&s_cnt[bb * 32 + lane], c);
                     }
                 }
                 __syncthreads();
@@ -164,17 +204,18 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                 }
                 __syncthreads();
                 if (tid == 0) {
-                    // counts of one block may arrive over several member chunks
-                    const int before = m0 == 0 ? 0 : fwn[cb];
-                    fwn[cb] = before + s_newn;
-                    atomicAdd(&d.sc->ranked, s_newn);
+                    fwn[cb] = s_newn;
+                    atomicAdd(&d.sc->ranked, s_newn - s_base);
                 }
             }
         }
         // blocks that received no member in this front still need their count of new members
         if (tid == 0)
-            for (int cb = g.rank; cb < ncb; cb += g.size)
+            for (int r = 0;; ++r) {
+                const int cb = peel_block(r, g.rank, g.size, ncb);
+                if (cb < 0) break;
                 if (nall == 0 || s_pref[cb + 1] == 0) fwn[cb] = 0;
+            }
         if (!group_sync(d.sc, g.size, budget)) return;
         prev_total = total;
         total = ld_volatile(&d.sc->ranked);

@@ -72,6 +72,19 @@ def test_nd_rank_stops_at_last_needed_front(frac):
     assert np.all(r[ref > l] == emo.EMO_NOT_RANKED)
 
 
+def test_fronts_larger_than_member_chunk():
+    # fronts of 2000 to 9000 points: the peel stages the members of a front
+    # in chunks of 4096, and new members of one column block found in later
+    # chunks are appended after those of the earlier ones
+    F = np.concatenate([wl.front_points(9000, 3, "sphere", seed=50 + i) + np.float32(0.3 * i)
+                        for i in range(3)]).astype(np.float32)
+    ref = oracle.nd_sort_deb(F)
+    assert np.bincount(ref)[0] > 2 * 4096
+    r, last = _gpu.gpu_rank(F)
+    assert np.array_equal(r, ref) and last == ref.max()
+    _gpu.compare_select(F, wl.das_dennis(30, 3), 20000, seed=6)
+
+
 def test_nd_rank_total_order_many_fronts():
     t = np.arange(1200, dtype=np.float32)[::-1].copy()
     F = np.stack([t, t * 2, t + 1], axis=1)          # one point per front
