@@ -19,7 +19,63 @@
 
 namespace emo {
 
-constexpr int kPeelNH = 18;  // counter planes: 4 + 18 bits per column and warp
+constexpr int kPeelNH = 9;  // counter planes: 4 + 9 bits per column (a chunk holds <= 4096 members)
+constexpr int kPeelBits = 4 + kPeelNH;
+static_assert(kPeelChunk < (1 << kPeelBits), "column counter overflow");
+static_assert(kCoopThreads == 512, "the counter reduction tree assumes 16 warps");
+
+// Exact column counts of the CTA: the 16 warps' bit-sliced counters are added
+// in a tree (16 -> 8 -> 4 -> 2 -> 1, ripple-carry over the bit planes, through
+// `scratch`), then warp w unpacks bits 2w and 2w + 1 of every word:
+// s_cnt[b * 32 + w'] = count of column 32 w' + b. No atomics.
+__device__ __forceinline__ void peel_reduce_counts(const VCount<kPeelNH>& vc, uint32_t* scratch, int* s_cnt,
+                                                   int warp, int lane)
+{
+    uint32_t P[kPeelBits];
+    P[0] = vc.ones;
+    P[1] = vc.twos;
+    P[2] = vc.fours;
+    P[3] = vc.eights;
+#pragma unroll
+    for (int i = 0; i < kPeelNH; ++i) P[4 + i] = vc.hi[i];
+#pragma unroll 1
+    for (int half = 8; half >= 1; half >>= 1) {
+        if (warp >= half && warp < 2 * half) {
+#pragma unroll
+            for (int p = 0; p < kPeelBits; ++p) scratch[((warp - half) * kPeelBits + p) * 32 + lane] = P[p];
+        }
+        __syncthreads();
+        if (warp < half) {
+            uint32_t c = 0u;
+#pragma unroll
+            for (int p = 0; p < kPeelBits; ++p) {
+                const uint32_t q = scratch[(warp * kPeelBits + p) * 32 + lane];
+                const uint32_t x = P[p] ^ q;
+                const uint32_t sum = x ^ c;
+                c = (P[p] & q) | (c & x);
+                P[p] = sum;
+            }
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+#pragma unroll
+        for (int p = 0; p < kPeelBits; ++p) scratch[p * 32 + lane] = P[p];
+    }
+    __syncthreads();
+    uint32_t Q[kPeelBits];
+#pragma unroll
+    for (int p = 0; p < kPeelBits; ++p) Q[p] = scratch[p * 32 + lane];
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb) {
+        const int b = 2 * warp + bb;
+        int c = 0;
+#pragma unroll
+        for (int p = 0; p < kPeelBits; ++p) c |= (int)((Q[p] >> b) & 1u) << p;
+        s_cnt[b * 32 + lane] = c;
+    }
+    __syncthreads();
+}
 
 // Column block dealt to CTA `rank` of a group of G in round r (snake order
 // over the blocks from the last to the first); -1 past the end.
@@ -116,19 +172,33 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
         for (int m0 = 0; m0 < nall; m0 += kPeelChunk) {
             const int mc = min(kPeelChunk, nall - m0);
             __syncthreads();
-            for (int i = tid; i < mc; i += blockDim.x) {  // stage members m0 .. m0 + mc in block order
-                const int o = m0 + i;
-                int lo = 0, hi = last_cb;  // block with s_pref[blk] <= o < s_pref[blk + 1]
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_pref[mid] <= o) lo = mid;
-                    else hi = mid - 1;
+            // stage members m0 .. m0 + mc in block order, four per thread at a
+            // time so that their loads overlap
+            for (int i0 = tid; i0 < mc; i0 += 4 * blockDim.x) {
+                int src[4], p[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int o = m0 + i0 + u * blockDim.x;
+                    int lo = 0, hi = last_cb;  // block with s_pref[blk] <= o < s_pref[blk + 1]
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_pref[mid] <= o) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    src[u] = lo * kColBlock + (o - s_pref[lo]);
                 }
-                // stage (tile base of the member's row block, row): tile (rb, cb) is base + cb
-                const int p = __ldcg(&fr[(int64_t)lo * kColBlock + (o - s_pref[lo])]);
-                const int rb = p >> 5;
-                const uint32_t base = (uint32_t)(tiles_before(rb, ncb) - rb / 32);
-                s_mem[i] = (int)(base * 32u + (uint32_t)(p & 31));
+#pragma unroll
+                for (int u = 0; u < 4; ++u) p[u] = i0 + u * blockDim.x < mc ? __ldcg(&fr[src[u]]) : 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i < mc) {
+                        // (tile base of the member's row block, row): tile (rb, cb) is base + cb
+                        const int rb = p[u] >> 5;
+                        const uint32_t base = (uint32_t)(tiles_before(rb, ncb) - rb / 32);
+                        s_mem[i] = (int)(base * 32u + (uint32_t)(p[u] & 31));
+                    }
+                }
             }
             __syncthreads();
             for (int r = 0;; ++r) {
@@ -136,7 +206,6 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                 if (cb < 0) break;
                 const int nmem = min(mc, s_pref[cb + 1] - m0);  // staged members reaching cb
                 if (nmem <= 0) continue;
-                for (int q = tid; q < kColBlock; q += blockDim.x) s_cnt[q] = 0;
                 // new members of one block may arrive over several member chunks:
                 // append after those found in the earlier chunks of this front
                 if (tid == 0) s_base = s_newn = m0 == 0 ? 0 : fwn[cb];
@@ -181,14 +250,8 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                     st = (st + 1) % kPeelStages;
                 }
                 cp_async_wait<0>();  // no copy outlives the block (the tail batches were empty)
-                const int top = vc.top_plane();
-                if (top >= 0) {
-                    for (int bb = 0; bb < 32; ++bb) {
-                        const int c = vc.count_upto(bb, top);
-                        if (c) atomicAdd(&s_cnt[bb * 32 + lane], c);
-                    }
-                }
-                __syncthreads();
+                __syncthreads();     // every warp is done with its ring before the tree reuses it
+                peel_reduce_counts(vc, reinterpret_cast<uint32_t*>(s_dyn), s_cnt, warp, lane);
                 for (int q = tid; q < kColBlock; q += blockDim.x) {
                     const int dq = s_cnt[(q & 31) * 32 + (q >> 5)];
                     const int64_t s = (int64_t)cb * kColBlock + q;
