@@ -89,9 +89,23 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Front lists hold each member p as (tile base of its row block) * 32 + row,
+// with tile (rb, cb) = base + cb: the row segment of p in block cb is
+// D[((base + cb) * 32 + p % 32) * 32 ...].
+__device__ __forceinline__ int32_t peel_encode(int64_t p, int ncb)
+{
+    const int64_t rb = p >> 5;
+    const uint32_t base = (uint32_t)(tiles_before(rb, ncb) - rb / 32);
+    return (int32_t)(base * 32u + (uint32_t)(p & 31));
+}
 
 __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
 {
@@ -125,7 +139,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
             const int64_t s = (int64_t)cb * kColBlock + q;
             if (s < n2 && __ldcg(&d.cnt[s]) == 0) {
                 const int slot = atomicAdd(&s_newn, 1);
-                d.front[(int64_t)cb * kColBlock + slot] = (int32_t)s;
+                d.front[(int64_t)cb * kColBlock + slot] = peel_encode(s, ncb);
                 d.rank_s[s] = 0;
             }
         }
@@ -172,34 +186,15 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
         for (int m0 = 0; m0 < nall; m0 += kPeelChunk) {
             const int mc = min(kPeelChunk, nall - m0);
             __syncthreads();
-            // stage members m0 .. m0 + mc in block order, four per thread at a
-            // time so that their loads overlap
-            for (int i0 = tid; i0 < mc; i0 += 4 * blockDim.x) {
-                int src[4], p[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int o = m0 + i0 + u * blockDim.x;
-                    int lo = 0, hi = last_cb;  // block with s_pref[blk] <= o < s_pref[blk + 1]
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_pref[mid] <= o) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    src[u] = lo * kColBlock + (o - s_pref[lo]);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) p[u] = i0 + u * blockDim.x < mc ? __ldcg(&fr[src[u]]) : 0;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = i0 + u * blockDim.x;
-                    if (i < mc) {
-                        // (tile base of the member's row block, row): tile (rb, cb) is base + cb
-                        const int rb = p[u] >> 5;
-                        const uint32_t base = (uint32_t)(tiles_before(rb, ncb) - rb / 32);
-                        s_mem[i] = (int)(base * 32u + (uint32_t)(p[u] & 31));
-                    }
-                }
+            // stage the (encoded) members m0 .. m0 + mc in block order: warp w
+            // copies the lists of blocks w, w + NW, ... with async 4-byte copies
+            for (int c = warp; c <= last_cb; c += NW) {
+                const int b0 = s_pref[c], lo = max(b0, m0), hi = min(s_pref[c + 1], m0 + mc);
+                for (int o = lo + lane; o < hi; o += 32)
+                    cp_async4(smem_u32(s_mem + (o - m0)), fr + (int64_t)c * kColBlock + (o - b0));
             }
+            cp_async_commit();
+            cp_async_wait<0>();
             __syncthreads();
             for (int r = 0;; ++r) {
                 const int cb = peel_block(r, g.rank, g.size, ncb);
@@ -209,6 +204,13 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                 // new members of one block may arrive over several member chunks:
                 // append after those found in the earlier chunks of this front
                 if (tid == 0) s_base = s_newn = m0 == 0 ? 0 : fwn[cb];
+                // the block's counts, loaded now and used after the stream
+                int cpre[kColBlock / kCoopThreads];
+#pragma unroll
+                for (int u = 0; u < kColBlock / kCoopThreads; ++u) {
+                    const int64_t sq = (int64_t)cb * kColBlock + tid + u * kCoopThreads;
+                    cpre[u] = sq < n2 ? __ldcg(&d.cnt[sq]) : 0;
+                }
                 __syncthreads();
                 VCount<kPeelNH> vc;
                 // copies of the warp's batches b = warp, warp + NW, ... (32 members each):
@@ -252,15 +254,17 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                 cp_async_wait<0>();  // no copy outlives the block (the tail batches were empty)
                 __syncthreads();     // every warp is done with its ring before the tree reuses it
                 peel_reduce_counts(vc, reinterpret_cast<uint32_t*>(s_dyn), s_cnt, warp, lane);
-                for (int q = tid; q < kColBlock; q += blockDim.x) {
+#pragma unroll
+                for (int u = 0; u < kColBlock / kCoopThreads; ++u) {
+                    const int q = tid + u * kCoopThreads;
                     const int dq = s_cnt[(q & 31) * 32 + (q >> 5)];
                     const int64_t s = (int64_t)cb * kColBlock + q;
                     if (dq && s < n2) {
-                        const int c = d.cnt[s] - dq;
+                        const int c = cpre[u] - dq;
                         d.cnt[s] = c;
                         if (c == 0) {
                             const int slot = atomicAdd(&s_newn, 1);
-                            fw[(int64_t)cb * kColBlock + slot] = (int32_t)s;
+                            fw[(int64_t)cb * kColBlock + slot] = peel_encode(s, ncb);
                             d.rank_s[s] = k + 1;
                         }
                     }
