@@ -168,7 +168,9 @@ __host__ __device__ __forceinline__ int64_t tile_index(int64_t rb, int64_t cb, i
 // Column-block prefix sets of the dominance kernel. Each 1024-column block
 // is split into two halves of 512 columns. For each key objective k
 // (objectives 2..m) the block stores:
-//   fv   -- the block's 1024 values of f_k sorted descending;
+//   fv   -- the block's 1024 values of f_k sorted descending (entry i at
+//           slot i ^ ((i / 32) % 32), which spreads a binary search's
+//           candidates over the shared-memory banks);
 //   cum0 -- cum0[j] = how many of the first j entries of fv lie in half 0
 //           (so a count j of values >= x splits into cum0[j] and j - cum0[j]);
 //   pb   -- for each half, the bitsets of its first c * cps columns in the

@@ -89,6 +89,9 @@ __device__ __forceinline__ void flush_counts(VCount<NH>& vlo, VCount<NH>& vhi, i
 }
 
 // ------------------------------------------------------------ k_colprep
+// Slot of entry i of a block's descending values (bank-spreading swizzle).
+__device__ __forceinline__ int fv_slot(int i) { return i ^ ((i >> 5) & 31); }
+
 // Entries of a descending array of 512 floats that are >= x (strict: > x).
 template <bool STRICT>
 __device__ __forceinline__ int count_before512(const float* v, float x)
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
                 const float x = s_v[q];
                 const int rank = (q & (kHalf - 1)) +
                                  (q < kHalf ? count_before512<true>(s_v + kHalf, x) : count_before512<false>(s_v, x));
-                fv[rank] = x;
+                fv[fv_slot(rank)] = x;
                 s_mark[rank] = q < kHalf;
             }
             // interleaved prefix bitsets: lane w builds word w from the sorted
@@ -214,15 +217,18 @@ struct PrefSmem {
 
 // Packed counts of the block's values >= x in both halves of one objective:
 // t0 | t1 << 16 (binary search over the full descending order, then the
-// half-0 share of that prefix).
+// half-0 share of that prefix). Entry i of the order is stored at fv_slot(i):
+// the candidates of one search level are i = c * step - 1 for step >= 32, all
+// with the same low five bits, and the XOR with i / 32 puts them in distinct
+// shared-memory banks.
 __device__ __forceinline__ int count_ge_halves(const unsigned char* ob, float x)
 {
     const float* fv = reinterpret_cast<const float*>(ob);
     int pos = 0;
 #pragma unroll
     for (int step = kColBlock / 2; step > 0; step >>= 1)
-        if (fv[pos + step - 1] >= x) pos += step;
-    if (fv[pos] >= x) ++pos;
+        if (fv[fv_slot(pos + step - 1)] >= x) pos += step;
+    if (fv[fv_slot(pos)] >= x) ++pos;
     const int t0 = reinterpret_cast<const uint16_t*>(ob + kPrefCumOff)[pos];
     return t0 | ((pos - t0) << 16);
 }
