@@ -120,6 +120,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM traffic of k_dom_pref<3> per byte of stored tiles, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum of one launch at
+# 2N=100,000, M=3: 15.80 MB read + 575.10 MB written for 635.79 MB of tiles).
+# The kernel's reads (prefix sets, keys) and writes (tiles) grow with the tiles
+# it writes, so the bench scales it by the timed workload's tile bytes. It is
+# reported only while the kernel sources are the ones it was measured on.
+DOM_TRAFFIC_PER_TILE_BYTE = (15_796_224 + 575_102_208) / 635_785_216
+DOM_TRAFFIC_SOURCES_SHA1 = "d4df74551b0e70501a88b24ac14513551d154490"
+DOM_SOURCES = ("k_dominance.cu", "emo_kernels.cuh", "emo_internal.cuh")
+
+
+def dom_sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in DOM_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2503_20286_gb300", "csrc", f),
+                  "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def triangle_tile_bytes(n2: int) -> int:
     """Bytes of the stored triangle of D: 4 KB tiles (rb, cb) with cb >= rb / 32."""
     nrb, ncb = -(-n2 // 32), -(-n2 // 1024)
@@ -335,7 +356,10 @@ def main():
         "stage_ms": {k: statistics.mean(v) for k, v in stage_ms.items()},
         "roofline": {"bound": "hbm", "kernel": f"k_dom_pref<{M}>", "achieved": achieved,
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                     "traffic": None, "algorithmic_bytes": tile_bytes,
+                     "traffic": (DOM_TRAFFIC_PER_TILE_BYTE * tile_bytes
+                                 if M == 3 and dom_sources_sha1() == DOM_TRAFFIC_SOURCES_SHA1 else None),
+                     "traffic_source": "ncu dram bytes at 2N=100k scaled by tile bytes",
+                     "algorithmic_bytes": tile_bytes,
                      "peak_source": f"{pk['source']} HBM copy bandwidth"},
         "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(F.nbytes + R.nbytes), "d2h_bytes_per_step": int(n_keep * 4)},
