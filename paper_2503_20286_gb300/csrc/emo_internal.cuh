@@ -34,7 +34,7 @@ constexpr int kMaxBatch = EMO_MAX_BATCH;
 constexpr int kTileRows = 32;         // rows per row block
 constexpr int kTileWords = 32;        // words per tile row
 constexpr int kColBlock = 1024;       // columns per column block
-constexpr int kDomRowChunk = 256;     // row blocks per dominance work item
+constexpr int kDomRowChunk = 512;     // row blocks per dominance work item
 constexpr int kCoopThreads = 512;     // threads of the cooperative kernels
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
@@ -285,14 +285,16 @@ __host__ __device__ __forceinline__ int64_t dom_items_of_cb(int64_t cb, int64_t 
     int64_t rbs = nrb < 32 * (cb + 1) ? nrb : 32 * (cb + 1);
     return cdiv(rbs, kDomRowChunk);
 }
-// Items of column blocks 0 .. c-1 in closed form: block cb < nrb / 32 has
-// cb / 8 + 1 items (its 32 (cb + 1) row blocks in chunks of 256), every later
-// block has cdiv(nrb, 256).
-static_assert(kDomRowChunk == 256, "dom_items_prefix assumes 8 column blocks of rows per chunk");
+// Items of column blocks 0 .. c-1 in closed form: with B = kDomRowChunk / 32
+// column blocks' worth of row blocks per item, block cb < nrb / 32 has
+// cb / B + 1 items (its 32 (cb + 1) row blocks in chunks of kDomRowChunk),
+// every later block has cdiv(nrb, kDomRowChunk).
+static_assert(kDomRowChunk % 32 == 0 && (kDomRowChunk / 32) % 2 == 0, "dom_items_prefix assumes an even B");
 __host__ __device__ __forceinline__ int64_t dom_items_prefix(int64_t c, int64_t nrb)
 {
-    const int64_t A = nrb / 32, a = c < A ? c : A, q = a >> 3, r = a & 7;
-    return (q + 1) * (4 * q + r) + (c > A ? (c - A) * cdiv(nrb, kDomRowChunk) : 0);
+    constexpr int64_t B = kDomRowChunk / 32;
+    const int64_t A = nrb / 32, a = c < A ? c : A, q = a / B, r = a % B;
+    return (q + 1) * (B / 2 * q + r) + (c > A ? (c - A) * cdiv(nrb, kDomRowChunk) : 0);
 }
 __host__ __device__ inline int64_t dom_items_of(int64_t n2)
 {

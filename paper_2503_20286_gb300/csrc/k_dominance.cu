@@ -26,7 +26,7 @@
 
 namespace emo {
 
-constexpr int kDomNH = 5;  // high count planes: up to 511 rows per lane and item
+constexpr int kDomNH = 6;  // high count planes: up to 1023 rows per lane and item
 static_assert(kDomRowChunk / 16 * 16 < (1 << (4 + kDomNH)), "column counter overflow");
 constexpr long long kCopyWaitCycles = 1ll << 32;
 constexpr int kHalf = kColBlock / 2;
@@ -284,7 +284,8 @@ __device__ __forceinline__ void pref_rows(const unsigned char* __restrict__ obj,
                                           VCount<kDomNH>& vlo, VCount<kDomNH>& vhi, int lane)
 {
     using S = PrefShape<K>;
-    const int l = lane & 15, h = lane >> 4, hs = (l >> 3) * 16;
+    const int l = lane & 15, h = lane >> 4;
+    const unsigned psel = (l >> 3) ? 0x4432u : 0x4410u;  // byte selector of the lane's half count
     unsigned long long* dst = reinterpret_cast<unsigned long long*>(tile + h * 16 * 32) + l;
 #pragma unroll 1
     for (int g = 0; g < 2; ++g) {
@@ -295,7 +296,7 @@ __device__ __forceinline__ void pref_rows(const unsigned char* __restrict__ obj,
             unsigned long long word = ~0ull;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const int tk = (__shfl_sync(0xffffffffu, t[k], i) >> hs) & 0xFFFF;
+                const int tk = (int)__byte_perm((unsigned)__shfl_sync(0xffffffffu, t[k], i), 0u, psel);
                 word &= prefix_word<S::LOG_CPS, S::ORD_OFF>(obj + k * S::OBJ_BYTES, tk, l);
             }
             word = row_masks<DIAG, DUP>(word, rowbase + i, cbase, rs, l);
