@@ -34,7 +34,7 @@ constexpr int kMaxBatch = EMO_MAX_BATCH;
 constexpr int kTileRows = 32;         // rows per row block
 constexpr int kTileWords = 32;        // words per tile row
 constexpr int kColBlock = 1024;       // columns per column block
-constexpr int kDomRowChunk = 512;     // row blocks per dominance work item
+constexpr int kDomRowChunk = 1024;    // row blocks per dominance work item
 constexpr int kCoopThreads = 512;     // threads of the cooperative kernels
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;

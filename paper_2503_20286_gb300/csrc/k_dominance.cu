@@ -26,7 +26,7 @@
 
 namespace emo {
 
-constexpr int kDomNH = 6;  // high count planes: up to 1023 rows per lane and item
+constexpr int kDomNH = 7;  // high count planes: up to 2047 rows per lane and item
 static_assert(kDomRowChunk / 16 * 16 < (1 << (4 + kDomNH)), "column counter overflow");
 constexpr long long kCopyWaitCycles = 1ll << 32;
 constexpr int kHalf = kColBlock / 2;
