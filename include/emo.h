@@ -171,8 +171,9 @@ emo_status emo_nsga3_select_batch(const emo_problem* descs, int32_t batch, void*
  * that must not enter an allocator, a fixed memory budget). The paper has no
  * counterpart; this is a deployment convenience. The selection runs in an
  * 8 MiB scratch array built into the library (held on every GPU that loads
- * it until the process exits); populations with n2 <= 8192 and n_r <= 8192
- * (any m <= 16) always fit, larger ones return EMO_ERR_WORKSPACE. The call
+ * it until the process exits); populations with n2 <= 7168 and n_r <= 7168
+ * (any m <= 16), or n2 <= 8192 and n_r <= 8192 (m <= 8), always fit on
+ * devices with up to 304 SMs; what does not fit returns EMO_ERR_WORKSPACE. The call
  * makes no device allocation. Its first call on a device looks up the
  * scratch address (cudaGetSymbolAddress) and should come before any stream
  * capture. Calls share the scratch: every call initialises what it reads,

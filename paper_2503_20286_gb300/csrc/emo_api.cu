@@ -97,9 +97,9 @@ DevInfo dev_info()
         int occ = 2;
         // k_peel takes peel_smem_bytes(ncb) of dynamic shared memory, the others none
         const void* kernels[] = {(const void*)k_sort, (const void*)k_peel, (const void*)k_stats,
-                                 (const void*)k_csr, (const void*)k_finish};
-        const int dyn[] = {0, kPeelDynSmem, 0, 0, 0};
-        for (int i = 0; i < 5; ++i) {
+                                 (const void*)k_csr, (const void*)k_niche, (const void*)k_finish};
+        const int dyn[] = {0, kPeelDynSmem, 0, 0, 0, 0};
+        for (int i = 0; i < (int)(sizeof(dyn) / sizeof(dyn[0])); ++i) {
             int o = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernels[i], kCoopThreads, dyn[i]) != cudaSuccess)
                 return DevInfo{};
@@ -211,8 +211,7 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
         sm.mark("rescan");
         if (coop((const void*)k_csr, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
         sm.mark("csr");
-        k_niche<<<nprob, 1024, 0, s>>>(plan);
-        if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
+        if (coop((const void*)k_niche, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
         sm.mark("niche");
     }
     if (coop((const void*)k_finish, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
@@ -381,7 +380,7 @@ int32_t emo_device_report(char* buf, int32_t len)
     struct K { const char* name; const void* fn; int dyn; };
     const K ks[] = {{"k_sort", (const void*)k_sort, 0}, {"k_peel", (const void*)k_peel, kPeelDynSmem},
                     {"k_stats", (const void*)k_stats, 0}, {"k_csr", (const void*)k_csr, 0},
-                    {"k_finish", (const void*)k_finish, 0}};
+                    {"k_niche", (const void*)k_niche, 0}, {"k_finish", (const void*)k_finish, 0}};
     for (const K& k : ks) {
         cudaFuncAttributes fa{};
         int occ = -1;

@@ -36,6 +36,7 @@ constexpr int kTileWords = 32;        // words per tile row
 constexpr int kColBlock = 1024;       // columns per column block
 constexpr int kDomRowChunk = 1024;    // row blocks per dominance work item
 constexpr int kCoopThreads = 512;     // threads of the cooperative kernels
+constexpr int kNicheBins = 4096;      // niching select: bins of the top 12 bits of a priority
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int64_t kMaxN2 = int64_t(1) << 21;
@@ -87,7 +88,8 @@ struct Scal {
     double a[kMaxM];
     unsigned int bar_count;
     unsigned int bar_gen;
-    int32_t pad_[2];
+    int32_t ncol;            // niching: keys collected from the selected histogram bin
+    int32_t pad_[1];
 };
 
 // Device-side descriptor with every workspace pointer of one problem.
@@ -122,6 +124,7 @@ struct ProbDev {
     int32_t* llist;          // [2][n2] last-front members (CSR order after sorting)
     int32_t* fen;            // [n2] Fenwick trees over each candidate list
     unsigned long long* ekeys;  // [n_r] priorities of the references in a level
+    int32_t* nhist;          // niching: [kNicheBins] key histogram | [G] packed per-CTA (min, count)
     int32_t* elist;          // [n_r] references served in a level
     int32_t* flag;           // [n2] survivor flags / scan scratch
     int32_t* hist;           // [G][256] radix histograms, reused by the scans
@@ -218,7 +221,8 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
     int64_t o_hist = take(int64_t(G) * kRadix * 4);
     int64_t o_flag = take((n2p + 1) * 4);
     int64_t o_pi = 0, o_d64 = 0, o_rhat = 0, o_flagged = 0, o_rho = 0, o_lcnt = 0, o_loff = 0,
-            o_llist = 0, o_fen = 0, o_ekeys = 0, o_elist = 0, o_rord = 0, o_rphi = 0, o_rsort = 0, o_fbound = 0;
+            o_llist = 0, o_fen = 0, o_ekeys = 0, o_elist = 0, o_rord = 0, o_rphi = 0, o_rsort = 0, o_fbound = 0,
+            o_nhist = 0;
     if (in.mode == MODE_SELECT) {
         o_pi = take(n2 * 4);
         o_d64 = take(n2 * 8);
@@ -235,6 +239,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         o_rphi = take(nr * 4);
         o_rsort = take(nr * m * 4);
         o_fbound = take(n2 * 4);
+        o_nhist = take(kNicheBins * 4 + int64_t(G) * 8);
     }
     int64_t o_colpre = take(ncb * (m - 1) * colprep_obj_bytes((int)(m - 1)));
     int64_t o_D = take(ntiles * 4096);
@@ -268,6 +273,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         d->fen = in.mode == MODE_SELECT ? (int32_t*)(base + o_fen) : nullptr;
         d->ekeys = in.mode == MODE_SELECT ? (unsigned long long*)(base + o_ekeys) : nullptr;
         d->elist = in.mode == MODE_SELECT ? (int32_t*)(base + o_elist) : nullptr;
+        d->nhist = in.mode == MODE_SELECT ? (int32_t*)(base + o_nhist) : nullptr;
         d->rord = in.mode == MODE_SELECT ? (int32_t*)(base + o_rord) : nullptr;
         d->rphi = in.mode == MODE_SELECT ? (float*)(base + o_rphi) : nullptr;
         d->rsort = in.mode == MODE_SELECT ? (float*)(base + o_rsort) : nullptr;

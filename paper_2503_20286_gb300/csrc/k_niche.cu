@@ -101,94 +101,187 @@ __device__ __forceinline__ void fen_remove(int32_t* fen, int n, int slot)
 }
 
 // ------------------------------------------------------------ k_niche
-constexpr int kNicheThreads = 1024;
+// One cooperative launch; the references of a problem are spread over its CTA
+// group, and a reference's list, Fenwick tree and counts are touched by one
+// thread only. Per level:
+//   (A) every CTA: the minimum niche count over its live references and how
+//       many hold it; the histogram of (C) is cleared;
+//   (B) every CTA: the group's minimum c and its count from the partials; if
+//       the level cannot be served in full, the histogram of the top 12 bits
+//       of the level's priorities (x0, j);
+//   (C) every CTA: the bin holding the `remaining`-th smallest priority; the
+//       keys of that bin are collected;
+//   (D) every CTA: the threshold (that priority, selected from the collected
+//       keys) and the picks of its references.
+// Every phase ends with a bounded group barrier; levels served in full skip
+// (B)'s histogram and (C).
+constexpr int kNicheSmallSel = 2048;  // collected keys ranked in shared memory
 
-__global__ void __launch_bounds__(kNicheThreads, 1) k_niche(Plan* plan)
+__device__ __forceinline__ unsigned long long niche_key(uint64_t seed, uint64_t gen, int64_t j, int c)
+{
+    return ((unsigned long long)niche_random(seed, gen, (uint32_t)j, (uint32_t)c, 0u) << 32) | (unsigned)j;
+}
+
+__global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
 {
     __shared__ int s_warp[33];
+    __shared__ unsigned long long s_keys[kNicheSmallSel];
     __shared__ int s_hist[kRadix];
-    __shared__ int s_ne;
-    __shared__ unsigned long long s_prefix;
-    __shared__ int s_k;
-    const ProbDev& d = plan->p[blockIdx.x];
+    __shared__ unsigned long long s_prefix, s_thresh;
+    __shared__ int s_k, s_bin, s_kbin;
+    const Group g = group_of(plan);
+    const ProbDev& d = plan->p[g.prob];
     const ProbIn& in = d.in;
+    const long long budget = plan->spin_budget;
     if (in.mode != MODE_SELECT || ld_volatile(&d.sc->status) != 0) return;
     Scal* sc = d.sc;
     const int tid = threadIdx.x;
     const int nr = in.n_r;
-    const int nP = sc->nP, nL = sc->nL;
+    const int nP = ld_volatile(&sc->nP), nL = ld_volatile(&sc->nL);
     const int K = (int)(in.n_keep - nP);
-    const int32_t* L = d.llist + (int64_t)sc->lbuf * in.n2;
+    const int32_t* L = d.llist + (int64_t)ld_volatile(&sc->lbuf) * in.n2;
     const uint64_t seed = in.seed, gen = in.gen;
+    const int64_t t0 = (int64_t)g.rank * blockDim.x + tid;
+    const int64_t stride = (int64_t)g.size * blockDim.x;
+    int32_t* hist = d.nhist;
+    unsigned long long* part = reinterpret_cast<unsigned long long*>(d.nhist + kNicheBins);
 
     if (K == nL) {  // the whole last front survives
-        for (int t = tid; t < nL; t += blockDim.x) d.flag[L[t]] = 1;
-        if (tid == 0) sc->levels = 0;
+        for (int64_t t = t0; t < nL; t += stride) d.flag[L[t]] = 1;
+        if (g.rank == 0 && tid == 0) sc->levels = 0;
         return;
     }
     int remaining = K, levels = 0;
     while (remaining > 0) {
-        int cmin = INT32_MAX;
-        for (int j = tid; j < nr; j += blockDim.x)
-            if (d.lcnt[j] > 0) cmin = min(cmin, d.rho[j]);
-        cmin = block_reduce_min<kNicheThreads>(cmin, s_warp);
-        if (cmin == INT32_MAX) {  // no live reference although picks remain
-            if (tid == 0) set_status(sc, EMO_ERR_INVALID_ARG);
+        // (A) this CTA's minimum niche count over live references, and its count
+        int cmin = INT32_MAX, cnt = 0;
+        for (int64_t j = t0; j < nr; j += stride) {
+            if (__ldcg(&d.lcnt[j]) > 0) {
+                const int r = __ldcg(&d.rho[j]);
+                if (r < cmin) {
+                    cmin = r;
+                    cnt = 1;
+                } else if (r == cmin) {
+                    ++cnt;
+                }
+            }
+        }
+        const int bmin = block_reduce_min<kCoopThreads>(cmin, s_warp);
+        const int bcnt = block_reduce_sum<kCoopThreads>(cmin == bmin ? cnt : 0, s_warp);
+        if (tid == 0) part[g.rank] = ((unsigned long long)(unsigned)bmin << 32) | (unsigned)bcnt;
+        for (int64_t b = t0; b < kNicheBins; b += stride) hist[b] = 0;
+        if (g.rank == 0 && tid == 0) sc->ncol = 0;
+        if (!group_sync(sc, g.size, budget)) return;
+
+        // (B) the level: minimum c over the group and the number of references holding it
+        int lm = INT32_MAX;
+        for (int r = tid; r < g.size; r += blockDim.x) lm = min(lm, (int)(__ldcg(&part[r]) >> 32));
+        const int c = block_reduce_min<kCoopThreads>(lm, s_warp);
+        if (c == INT32_MAX) {  // no live reference although picks remain
+            if (g.rank == 0 && tid == 0) set_status(sc, EMO_ERR_INVALID_ARG);
             return;
         }
-        int ne = 0;
-        for (int j = tid; j < nr; j += blockDim.x) ne += (d.lcnt[j] > 0 && d.rho[j] == cmin) ? 1 : 0;
-        ne = block_reduce_sum<kNicheThreads>(ne, s_warp);
+        int lc = 0;
+        for (int r = tid; r < g.size; r += blockDim.x) {
+            const unsigned long long v = __ldcg(&part[r]);
+            if ((int)(v >> 32) == c) lc += (int)(v & 0xFFFFFFFFull);
+        }
+        const int ne = block_reduce_sum<kCoopThreads>(lc, s_warp);
         const bool all = ne <= remaining;
         unsigned long long thresh = ~0ull;
         if (!all) {
             // priorities of the level's references; keep the `remaining` smallest
-            if (tid == 0) s_ne = 0;
-            __syncthreads();
-            for (int j = tid; j < nr; j += blockDim.x)
-                if (d.lcnt[j] > 0 && d.rho[j] == cmin) {
-                    const unsigned long long key =
-                        ((unsigned long long)niche_random(seed, gen, (uint32_t)j, (uint32_t)cmin, 0u) << 32) |
-                        (unsigned)j;
-                    d.ekeys[atomicAdd(&s_ne, 1)] = key;
+            for (int64_t j = t0; j < nr; j += stride)
+                if (__ldcg(&d.lcnt[j]) > 0 && __ldcg(&d.rho[j]) == c)
+                    atomicAdd(&hist[niche_key(seed, gen, j, c) >> 52], 1);
+            if (!group_sync(sc, g.size, budget)) return;
+
+            // (C) the bin of the priority of rank remaining - 1 (each thread scans 8 bins)
+            {
+                constexpr int PER = kNicheBins / kCoopThreads;
+                int h[PER], v = 0;
+#pragma unroll
+                for (int e = 0; e < PER; ++e) {
+                    h[e] = __ldcg(&hist[tid * PER + e]);
+                    v += h[e];
                 }
-            __syncthreads();
-            if (tid == 0) { s_prefix = 0ull; s_k = remaining - 1; }
-            unsigned long long mask = 0ull;
-            for (int shift = 56; shift >= 0; shift -= 8) {
-                for (int i = tid; i < kRadix; i += blockDim.x) s_hist[i] = 0;
-                __syncthreads();
-                const unsigned long long prefix = s_prefix;
-                for (int e = tid; e < s_ne; e += blockDim.x) {
-                    const unsigned long long key = d.ekeys[e];
-                    if ((key & mask) == prefix) atomicAdd(&s_hist[(key >> shift) & 0xFF], 1);
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    int acc = 0, dg = 0;
-                    for (; dg < kRadix; ++dg) {
-                        if (acc + s_hist[dg] > s_k) break;
-                        acc += s_hist[dg];
+                int tot;
+                int pre = block_exclusive_scan<kCoopThreads>(v, s_warp, tot);
+                const int k = remaining - 1;
+                if (pre <= k && k < pre + v) {
+#pragma unroll
+                    for (int e = 0; e < PER; ++e) {
+                        if (k < pre + h[e]) {
+                            s_bin = tid * PER + e;
+                            s_kbin = k - pre;
+                            break;
+                        }
+                        pre += h[e];
                     }
-                    s_k -= acc;
-                    s_prefix = prefix | ((unsigned long long)dg << shift);
                 }
-                mask |= 0xFFull << shift;
                 __syncthreads();
             }
-            thresh = s_prefix;
-        }
-        for (int j = tid; j < nr; j += blockDim.x) {
-            const int len = d.lcnt[j];
-            if (len <= 0 || d.rho[j] != cmin) continue;
-            if (!all) {
-                const unsigned long long key =
-                    ((unsigned long long)niche_random(seed, gen, (uint32_t)j, (uint32_t)cmin, 0u) << 32) | (unsigned)j;
-                if (key > thresh) continue;
+            const int bin = s_bin, kbin = s_kbin;
+            for (int64_t j = t0; j < nr; j += stride)
+                if (__ldcg(&d.lcnt[j]) > 0 && __ldcg(&d.rho[j]) == c) {
+                    const unsigned long long key = niche_key(seed, gen, j, c);
+                    if ((int)(key >> 52) == bin) d.ekeys[atomicAdd(&sc->ncol, 1)] = key;
+                }
+            if (!group_sync(sc, g.size, budget)) return;
+
+            // (D) the kbin-th smallest collected key (keys are distinct: j is in the low bits)
+            const int nc = ld_volatile(&sc->ncol);
+            if (nc <= kNicheSmallSel) {
+                for (int i = tid; i < nc; i += blockDim.x) s_keys[i] = __ldcg(&d.ekeys[i]);
+                __syncthreads();
+                for (int i = tid; i < nc; i += blockDim.x) {
+                    const unsigned long long key = s_keys[i];
+                    int r = 0;
+                    for (int q = 0; q < nc; ++q) r += s_keys[q] < key ? 1 : 0;
+                    if (r == kbin) s_thresh = key;
+                }
+                __syncthreads();
+            } else {  // many keys in one bin: byte-wise radix select
+                if (tid == 0) {
+                    s_prefix = 0ull;
+                    s_k = kbin;
+                }
+                unsigned long long mask = 0ull;
+                for (int shift = 56; shift >= 0; shift -= 8) {
+                    for (int i = tid; i < kRadix; i += blockDim.x) s_hist[i] = 0;
+                    __syncthreads();
+                    const unsigned long long prefix = s_prefix;
+                    for (int e = tid; e < nc; e += blockDim.x) {
+                        const unsigned long long key = __ldcg(&d.ekeys[e]);
+                        if ((key & mask) == prefix) atomicAdd(&s_hist[(key >> shift) & 0xFF], 1);
+                    }
+                    __syncthreads();
+                    if (tid == 0) {
+                        int acc = 0, dg = 0;
+                        for (; dg < kRadix; ++dg) {
+                            if (acc + s_hist[dg] > s_k) break;
+                            acc += s_hist[dg];
+                        }
+                        s_k -= acc;
+                        s_prefix = prefix | ((unsigned long long)dg << shift);
+                    }
+                    mask |= 0xFFull << shift;
+                    __syncthreads();
+                }
+                if (tid == 0) s_thresh = s_prefix;
+                __syncthreads();
             }
+            thresh = s_thresh;
+        }
+
+        // picks: every level reference (all) or those with priority <= thresh
+        for (int64_t j = t0; j < nr; j += stride) {
+            const int len = d.lcnt[j];
+            if (len <= 0 || d.rho[j] != c) continue;
+            if (!all && niche_key(seed, gen, j, c) > thresh) continue;
             const int off = d.loff[j], full = d.loff[j + 1] - off;
             int pos;
-            if (cmin == 0) {
+            if (c == 0) {
                 // nearest member; the list is untouched at level 0
                 pos = 0;
                 double bd = d.d64[L[off]];
@@ -196,23 +289,27 @@ __global__ void __launch_bounds__(kNicheThreads, 1) k_niche(Plan* plan)
                 for (int t = 1; t < full; ++t) {
                     const int v = L[off + t];
                     const double dv = d.d64[v];
-                    if (dv < bd || (dv == bd && v < bi)) { bd = dv; bi = v; pos = t; }
+                    if (dv < bd || (dv == bd && v < bi)) {
+                        bd = dv;
+                        bi = v;
+                        pos = t;
+                    }
                 }
             } else {
-                const uint32_t u = niche_random(seed, gen, (uint32_t)j, (uint32_t)cmin, 1u);
+                const uint32_t u = niche_random(seed, gen, (uint32_t)j, (uint32_t)c, 1u);
                 const int rank = (int)(((unsigned long long)u * (unsigned long long)len) >> 32);
                 pos = fen_select(d.fen + off, full, rank);
             }
             d.flag[L[off + pos]] = 1;
             fen_remove(d.fen + off, full, pos);
             d.lcnt[j] = len - 1;
-            d.rho[j] = cmin + 1;
+            d.rho[j] = c + 1;
         }
-        __syncthreads();
+        if (!group_sync(sc, g.size, budget)) return;
         remaining -= all ? ne : remaining;
         ++levels;
     }
-    if (tid == 0) sc->levels = levels;
+    if (g.rank == 0 && tid == 0) sc->levels = levels;
 }
 
 // ------------------------------------------------------------ k_finish
