@@ -182,8 +182,8 @@ __global__ void k_prep(Plan* plan);
 __global__ void k_sort(Plan* plan);
 __global__ void k_peel(Plan* plan);
 
-constexpr int kPeelChunk = 4096;   // front members staged in shared memory at once
-constexpr int kPeelStages = 3;     // per-warp ring of 32-row copies in flight
+constexpr int kPeelChunk = 8192;   // front members staged in shared memory at once
+constexpr int kPeelStages = 2;     // per-warp ring of 32-row copies (one batch in flight while one is counted)
 constexpr int kPeelRingBytes = (kCoopThreads / 32) * kPeelStages * 32 * 128;
 // Dynamic shared memory of k_peel for ncb column blocks: the copy ring, the
 // member prefix per block and the staged members.

@@ -9,7 +9,7 @@
 // blocks of the mean). Per front, the CTA stages the members whose rows reach
 // its blocks in shared memory; for each owned block every warp copies the
 // 128-byte row segments of 32 members at a time into its own ring of
-// shared-memory stages with cp.async (two batches in flight while the third
+// shared-memory stages with cp.async (the next batch in flight while one
 // is counted), then adds the words into per-lane Harley-Seal bit-sliced
 // counters, giving d_j. Points whose count reaches zero form the next front.
 // One bounded group barrier separates fronts. Selection stops once the fronts
@@ -19,7 +19,7 @@
 
 namespace emo {
 
-constexpr int kPeelNH = 9;  // counter planes: 4 + 9 bits per column (a chunk holds <= 4096 members)
+constexpr int kPeelNH = 10;  // counter planes: 4 + 10 bits per column (a chunk holds <= 8192 members)
 constexpr int kPeelBits = 4 + kPeelNH;
 static_assert(kPeelChunk < (1 << kPeelBits), "column counter overflow");
 static_assert(kCoopThreads == 512, "the counter reduction tree assumes 16 warps");
@@ -231,11 +231,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                     cp_async_commit();
                 };
                 int b = warp, st = 0;
-                issue(b, 0);
-                issue(b + NW, 1);
+#pragma unroll
+                for (int q = 0; q + 1 < kPeelStages; ++q) issue(b + q * NW, q);
                 for (; b < nb; b += NW) {
-                    issue(b + 2 * NW, (st + 2) % kPeelStages);
-                    cp_async_wait<2>();
+                    issue(b + (kPeelStages - 1) * NW, (st + kPeelStages - 1) % kPeelStages);
+                    cp_async_wait<kPeelStages - 1>();
                     __syncwarp();
                     const uint32_t* src = ring + st * (32 * 32);
                     const int nrow = min(32, nmem - b * 32);
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                         for (int j = 0; j < 16; ++j) x[j] = j + 16 < nrow ? src[(j + 16) * 32 + lane] : 0u;
                         vc.add16(x);
                     }
-                    __syncwarp();  // the stage is refilled two iterations later
+                    __syncwarp();  // the stage is refilled kPeelStages - 1 iterations later
                     st = (st + 1) % kPeelStages;
                 }
                 cp_async_wait<0>();  // no copy outlives the block (the tail batches were empty)
