@@ -114,7 +114,8 @@ struct ProbDev {
     double* d64;             // [n2] perpendicular distance (FP64)
     float* rhat;             // [n_r][m] unit reference directions (FP32)
     int32_t* rord;           // [2][n_r] references sorted by polar angle from axis 1 (ping-pong)
-    float* rphi;             // [n_r] sorted polar angles
+    float* rphi;             // [n_r] sorted polar angles (from axis 1)
+    float* rphi2;            // [n_r] angles from axis 2, in the same order
     float* rsort;            // [n_r][m] unit directions in polar-angle order
     int32_t* flagged;        // [n2] points for the exhaustive FP64 scan
     float* flagged_bound;    // [n2] angular half-width of that scan (inf = all references)
@@ -222,7 +223,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
     int64_t o_flag = take((n2p + 1) * 4);
     int64_t o_pi = 0, o_d64 = 0, o_rhat = 0, o_flagged = 0, o_rho = 0, o_lcnt = 0, o_loff = 0,
             o_llist = 0, o_fen = 0, o_ekeys = 0, o_elist = 0, o_rord = 0, o_rphi = 0, o_rsort = 0, o_fbound = 0,
-            o_nhist = 0;
+            o_nhist = 0, o_rphi2 = 0;
     if (in.mode == MODE_SELECT) {
         o_pi = take(n2 * 4);
         o_d64 = take(n2 * 8);
@@ -237,6 +238,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         o_elist = take(nr * 4);
         o_rord = take(2 * nr * 4);
         o_rphi = take(nr * 4);
+        o_rphi2 = take(nr * 4);
         o_rsort = take(nr * m * 4);
         o_fbound = take(n2 * 4);
         o_nhist = take(kNicheBins * 4 + int64_t(G) * 8);
@@ -276,6 +278,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         d->nhist = in.mode == MODE_SELECT ? (int32_t*)(base + o_nhist) : nullptr;
         d->rord = in.mode == MODE_SELECT ? (int32_t*)(base + o_rord) : nullptr;
         d->rphi = in.mode == MODE_SELECT ? (float*)(base + o_rphi) : nullptr;
+        d->rphi2 = in.mode == MODE_SELECT ? (float*)(base + o_rphi2) : nullptr;
         d->rsort = in.mode == MODE_SELECT ? (float*)(base + o_rsort) : nullptr;
         d->flagged_bound = in.mode == MODE_SELECT ? (float*)(base + o_fbound) : nullptr;
         d->colpre = (unsigned char*)(base + o_colpre);
@@ -435,6 +438,14 @@ __device__ __forceinline__ float polar_angle(const float* v, int m)
     float s = 0.0f;
     for (int k = 1; k < m; ++k) s = fmaf(v[k], v[k], s);
     return atan2f(sqrtf(s), v[0]);
+}
+// Angle from axis 2, by the same formula (the second pivot of the association
+// index).
+__device__ __forceinline__ float polar_angle2(const float* v, int m)
+{
+    float s = v[0] * v[0];
+    for (int k = 2; k < m; ++k) s = fmaf(v[k], v[k], s);
+    return atan2f(sqrtf(s), v[1]);
 }
 
 // Niching stream: key = seed, counter = (j, 2 c + tag, generation).

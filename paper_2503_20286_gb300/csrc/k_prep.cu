@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
     for (int64_t s = (int64_t)g.rank * blockDim.x + threadIdx.x; s < nr; s += (int64_t)g.size * blockDim.x) {
         const int64_t j = __ldcg(&ro[s]);
         d.rphi[s] = polar_angle(rhat + j * m, m);
+        d.rphi2[s] = polar_angle2(rhat + j * m, m);
         for (int k = 0; k < m; ++k) d.rsort[s * m + k] = rhat[j * m + k];
     }
 }

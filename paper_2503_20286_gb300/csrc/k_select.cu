@@ -236,7 +236,9 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_stats(Plan* plan)
 // angle between two directions is at least the difference of their polar
 // angles (triangle inequality on the sphere), only references with
 // |phi_r - phi_f| <= theta_best + margin can beat the best one found so far.
-// The scan walks outward from phi_f and stops on that bound.
+// The scan walks outward from phi_f and stops on that bound. The same
+// inequality for the angle from axis 2 (a second pivot, stored per reference)
+// skips the distance of references on the far side of the band's ring.
 //
 // Error band of the FP32 distance (relative to |f|), two evaluations:
 // |delta d| <= (sqrt(m)(m + 10) + (m + 1)/2) u |f| each.
@@ -302,6 +304,7 @@ __global__ void __launch_bounds__(256) k_assoc_m(Plan* plan, int pfirst, int pla
         const int nS = ld_volatile(&sc->nS);
         const int nr = d.in.n_r;
         const float* __restrict__ rphi = d.rphi;
+        const float* __restrict__ rphi2 = d.rphi2;
         const float* __restrict__ rs = d.rsort;
         const int32_t* __restrict__ ro = d.rord + (int64_t)sc->rbuf * nr;
         const float band = assoc_band(M), margin = assoc_margin(M);
@@ -322,17 +325,28 @@ __global__ void __launch_bounds__(256) k_assoc_m(Plan* plan, int pfirst, int pla
                 continue;
             }
             const float phif = polar_angle(f, M);
+            const float phi2f = polar_angle2(f, M);
             float c1 = INFINITY, c2 = INFINITY, c3 = INFINITY;  // FP32 d^2, best three
             int s1 = -1, s2 = -1;                                 // sorted positions of the best two
             float bound = INFINITY;                               // angular half-width still to scan
             int L = lower_bound_f(rphi, nr, phif) - 1, Rp = L + 1;
+            float dl = L >= 0 ? phif - __ldg(&rphi[L]) : INFINITY;
+            float dr = Rp < nr ? __ldg(&rphi[Rp]) - phif : INFINITY;
             while (L >= 0 || Rp < nr) {  // at most n_r steps
-                const float dl = L >= 0 ? phif - __ldg(&rphi[L]) : INFINITY;
-                const float dr = Rp < nr ? __ldg(&rphi[Rp]) - phif : INFINITY;
                 const bool left = L >= 0 && (Rp >= nr || dl <= dr);
                 const float dm = left ? dl : dr;
                 if (!(dm <= bound)) break;
-                const int q = left ? L-- : Rp++;  // 0 <= q < n_r
+                int q;  // 0 <= q < n_r
+                if (left) {
+                    q = L--;
+                    dl = L >= 0 ? phif - __ldg(&rphi[L]) : INFINITY;
+                } else {
+                    q = Rp++;
+                    dr = Rp < nr ? __ldg(&rphi[Rp]) - phif : INFINITY;
+                }
+                // second pivot: the angle to the reference is at least the
+                // difference of the angles from axis 2 (same margins as axis 1)
+                if (M > 2 && !(fabsf(__ldg(&rphi2[q]) - phi2f) <= bound)) continue;
                 float u[M];
 #pragma unroll
                 for (int k = 0; k < M; ++k) u[k] = __ldg(&rs[(int64_t)q * M + k]);
