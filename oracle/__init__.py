@@ -62,6 +62,11 @@ def lib():
                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32,
                 ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
                 ctypes.POINTER(_Trace)]
+            _lib.oracle_nsga3_select_mode.restype = ctypes.c_int
+            _lib.oracle_nsga3_select_mode.argtypes = [
+                ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32,
+                ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
+                ctypes.POINTER(_Trace)]
             _lib.oracle_dominance_bits.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                                    ctypes.c_void_p, ctypes.c_int64]
             _lib.oracle_domination_counts.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
@@ -134,7 +139,12 @@ class OracleError(RuntimeError):
     pass
 
 
-def nsga3_select(F, R, n_keep: int, seed: int, generation: int = 0, trace: bool = True):
+NICHE_EXACT = 0    # niching of Algorithm S.1 (level form)
+NICHE_ONESHOT = 1  # one-shot niche selection of Algorithm S.4 + Update-Rank (Algorithm S.6)
+
+
+def nsga3_select(F, R, n_keep: int, seed: int, generation: int = 0, trace: bool = True,
+                 mode: int = NICHE_EXACT):
     """Survivor indices (ascending) and, with ``trace``, every intermediate."""
     F = _f32(F)
     R = _f32(R)
@@ -151,9 +161,9 @@ def nsga3_select(F, R, n_keep: int, seed: int, generation: int = 0, trace: bool 
                 "picked": np.zeros(n2, np.uint8)}
         for k, v in bufs.items():
             setattr(t, k, _p(v))
-    rc = lib().oracle_nsga3_select(_p(F), n2, m, _p(R), n_r, n_keep,
-                                   seed & 0xFFFFFFFFFFFFFFFF, generation & 0xFFFFFFFFFFFFFFFF,
-                                   _p(surv), ctypes.byref(t))
+    rc = lib().oracle_nsga3_select_mode(_p(F), n2, m, _p(R), n_r, n_keep,
+                                        seed & 0xFFFFFFFFFFFFFFFF, generation & 0xFFFFFFFFFFFFFFFF, int(mode),
+                                        _p(surv), ctypes.byref(t))
     if rc != 0:
         raise OracleError(f"oracle_nsga3_select status {rc}")
     out = dict(bufs)

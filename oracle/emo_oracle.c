@@ -37,6 +37,15 @@
  *     by the seed, counter (j, 2c + tag, generation)); all references at the
  *     current minimum niche count are served in one level.
  *   - Survivors are returned as ascending indices (Section IV-A, i_next).
+ *   - One-shot niching (the tensorized niche selection of Algorithm S.4 and
+ *     Update-Rank, Algorithm S.6), selected by mode 1: every reference with
+ *     niche count 0 and at least one last-front candidate takes its nearest
+ *     candidate (d, then index); with n_dif = K - (number taken), the first
+ *     n_dif of the remaining last-front points are added (n_dif > 0) or the
+ *     first -n_dif of the taken points are dropped (n_dif < 0). "First" is in
+ *     the order of the shuffled input in the paper; here it is the order of
+ *     Philox keys (x0 of counter (i, 0xFFFFFFF0 + tag, generation), tag 1 to
+ *     add, 2 to drop; ties by index).
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused.
  */
@@ -79,6 +88,21 @@ static uint32_t niche_random(uint64_t seed, uint64_t gen, int64_t j, int64_t c, 
     uint32_t ctr[4], key[2], out[4];
     ctr[0] = (uint32_t)j;
     ctr[1] = (uint32_t)(2 * c + tag);
+    ctr[2] = (uint32_t)(gen & 0xFFFFFFFFu);
+    ctr[3] = (uint32_t)(gen >> 32);
+    key[0] = (uint32_t)(seed & 0xFFFFFFFFu);
+    key[1] = (uint32_t)(seed >> 32);
+    oracle_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
+/* First output word of the one-shot stream for point i (Algorithm S.6's
+   fill / drop order; tag 1 = add, 2 = drop). */
+static uint32_t oneshot_random(uint64_t seed, uint64_t gen, int64_t i, int tag)
+{
+    uint32_t ctr[4], key[2], out[4];
+    ctr[0] = (uint32_t)i;
+    ctr[1] = 0xFFFFFFF0u + (uint32_t)tag;
     ctr[2] = (uint32_t)(gen & 0xFFFFFFFFu);
     ctr[3] = (uint32_t)(gen >> 32);
     key[0] = (uint32_t)(seed & 0xFFFFFFFFu);
@@ -301,10 +325,13 @@ static int solve_hyperplane(int m, const double* E_in, double* b)
     return 0;
 }
 
-int oracle_nsga3_select(const float* F, int64_t n2, int m, const float* R, int32_t n_r,
-                        int64_t n_keep, uint64_t seed, uint64_t gen,
-                        int32_t* survivors, oracle_trace* tr)
+/* mode 0: niching of Algorithm S.1 (level form); mode 1: one-shot niche
+   selection of Algorithm S.4 with Update-Rank (Algorithm S.6). */
+int oracle_nsga3_select_mode(const float* F, int64_t n2, int m, const float* R, int32_t n_r,
+                             int64_t n_keep, uint64_t seed, uint64_t gen, int mode,
+                             int32_t* survivors, oracle_trace* tr)
 {
+    if (mode != 0 && mode != 1) return ORACLE_EINVAL;
     if (!F || !R || !survivors || m < 2 || m > 16 || n_r < 1 || n2 < 1 || n_keep < 1 || n_keep > n2)
         return ORACLE_EINVAL;
     for (int64_t i = 0; i < n2 * m; ++i) if (!isfinite(F[i])) return ORACLE_ENONFINITE;
@@ -444,8 +471,42 @@ int oracle_nsga3_select(const float* F, int64_t n2, int m, const float* R, int32
 
     /* 10. Niching: serve every least-crowded live reference once per level. */
     for (int32_t j = 0; j < n_r; ++j) alive[j] = cnt[j] > 0;
-    int64_t remaining = K;
+    int64_t remaining = mode == 0 ? K : 0;
     int32_t levels = 0;
+    if (mode == 1) {
+        /* 10'. One-shot niche selection (Algorithm S.4): each reference with
+           rho_j = 0 and rho_{l,j} > 0 takes the last-front point of smallest
+           distance d associated with it (D' argmin; ties: lowest index). */
+        int64_t n_sel = 0;
+        for (int32_t j = 0; j < n_r; ++j) {
+            if (rho[j] != 0 || cnt[j] == 0) continue;
+            const int64_t* Cj = lst + off[j];
+            int64_t best = Cj[0];
+            for (int64_t q = 1; q < cnt[j]; ++q)
+                if (dist[Cj[q]] < dist[best] || (dist[Cj[q]] == dist[best] && Cj[q] < best)) best = Cj[q];
+            picked[best] = 1;
+            ++n_sel;
+        }
+        /* Update-Rank (Algorithm S.6): n_dif = n - n_s, n_s = |P| + n_sel. */
+        int64_t n_dif = K - n_sel;
+        int64_t nk = 0;
+        uint64_t* ord = (uint64_t*)malloc((size_t)(nL > 0 ? nL : 1) * sizeof(uint64_t));
+        if (!ord) goto done;
+        if (n_dif > 0) {            /* add the first n_dif remaining last-front points */
+            for (int64_t i = 0; i < n2; ++i)
+                if (rank[i] == l && !picked[i])
+                    ord[nk++] = ((uint64_t)oneshot_random(seed, gen, i, 1) << 32) | (uint64_t)i;
+            qsort(ord, (size_t)nk, sizeof(uint64_t), cmp_u64);
+            for (int64_t e = 0; e < n_dif; ++e) picked[ord[e] & 0xFFFFFFFFu] = 1;
+        } else if (n_dif < 0) {     /* drop the first -n_dif taken points */
+            for (int64_t i = 0; i < n2; ++i)
+                if (picked[i]) ord[nk++] = ((uint64_t)oneshot_random(seed, gen, i, 2) << 32) | (uint64_t)i;
+            qsort(ord, (size_t)nk, sizeof(uint64_t), cmp_u64);
+            for (int64_t e = 0; e < -n_dif; ++e) picked[ord[e] & 0xFFFFFFFFu] = 0;
+        }
+        free(ord);
+        levels = 1;
+    }
     while (remaining > 0) {
         int64_t c = INT64_MAX;
         for (int32_t j = 0; j < n_r; ++j) if (alive[j] && rho[j] < c) c = rho[j];
@@ -511,4 +572,11 @@ done:
     free(rank); free(sorted); free(inS); free(fn); free(pi); free(dist); free(rho);
     free(cnt); free(off); free(lst); free(picked); free(alive); free(E); free(keyed);
     return status;
+}
+
+int oracle_nsga3_select(const float* F, int64_t n2, int m, const float* R, int32_t n_r,
+                        int64_t n_keep, uint64_t seed, uint64_t gen,
+                        int32_t* survivors, oracle_trace* tr)
+{
+    return oracle_nsga3_select_mode(F, n2, m, R, n_r, n_keep, seed, gen, 0, survivors, tr);
 }

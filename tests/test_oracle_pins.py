@@ -18,6 +18,10 @@ off-by-one in l, a wrong Philox constant, a wrong pivot rule...) fails here:
   orthogonal to R_j gives distance delta ||u||.
 * Niching equals a literal one-pick-at-a-time run of Algorithm S.1 that
   breaks ties by the same random priorities.
+* One-shot niching (Algorithm S.4 + Update-Rank, Algorithm S.6): when the
+  number of empty niches with candidates equals K, it selects exactly what
+  the level form selects at its only level (a separate code path); adding
+  or dropping points follows a plain sort of the Philox keys.
 """
 import itertools
 import math
@@ -332,3 +336,62 @@ def test_golden_config0():
     assert " ".join(map(str, surv.tolist())) == gold["survivors"]
     assert " ".join(map(str, t["rank"].tolist())) == gold["rank"]
     assert int(gold["last_rank"]) == t["last_rank"]
+
+
+def _oneshot_key(seed, gen, i, tag):
+    ctr = [i & 0xFFFFFFFF, 0xFFFFFFF0 + tag, gen & 0xFFFFFFFF, gen >> 32]
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    return (int(oracle.philox4x32_10(ctr, key)[0]) << 32) | i
+
+
+def _empty_niche_case(idx):
+    """A population and the n_keep at which K equals the number of empty
+    niches holding last-front candidates (E0), with the level-form trace."""
+    rng = np.random.default_rng(700 + idx)
+    m = int(rng.integers(2, 5))
+    n2 = int(rng.integers(120, 400))
+    F = wl.population(n2, m, m + 4, "sphere" if idx % 2 else "linear", seed=900 + idx)
+    if idx >= 4:
+        F = (np.round(F * 16) / 16).astype(np.float32)   # ties and duplicates
+    R = wl.das_dennis(wl.h_for_count(n2 // 2, m), m)   # about n2 / 2 references: many empty niches
+    seed, gen = int(rng.integers(0, 2 ** 63)), int(rng.integers(0, 2 ** 40))
+    n_keep = int(rng.integers(n2 // 4, 3 * n2 // 4))
+    _, t = oracle.nsga3_select(F, R, n_keep, seed, gen)
+    l, nP = t["last_rank"], t["n_before"]
+    L = np.flatnonzero(t["rank"] == l)
+    E0 = np.unique(t["pi"][L][t["rho"][t["pi"][L]] == 0])
+    return F, R, seed, gen, nP, len(L), len(E0)
+
+
+@pytest.mark.parametrize("idx", range(6))
+def test_oneshot_equals_level_form_when_empty_niches_fill_k(idx):
+    F, R, seed, gen, nP, nL, nE0 = _empty_niche_case(idx)
+    if nE0 == 0:
+        pytest.skip("no empty niche with candidates")
+    n_keep = nP + nE0   # K = |E0|: one level of nearest picks, no add, no drop
+    s0, t0 = oracle.nsga3_select(F, R, n_keep, seed, gen, mode=oracle.NICHE_EXACT)
+    s1, t1 = oracle.nsga3_select(F, R, n_keep, seed, gen, mode=oracle.NICHE_ONESHOT)
+    assert t0["n_levels"] == 1 and t0["n_before"] == nP
+    assert np.array_equal(s0, s1)
+
+
+@pytest.mark.parametrize("idx", range(6))
+def test_oneshot_add_and_drop_follow_philox_order(idx):
+    F, R, seed, gen, nP, nL, nE0 = _empty_niche_case(idx)
+    if nE0 < 4 or nL - nE0 < 4:
+        pytest.skip("too few empty niches or remaining candidates")
+    base, t = oracle.nsga3_select(F, R, nP + nE0, seed, gen, mode=oracle.NICHE_EXACT)
+    Q = np.setdiff1d(base, np.flatnonzero(t["rank"] < t["last_rank"]))
+    P = np.flatnonzero(t["rank"] < t["last_rank"])
+    L = np.flatnonzero(t["rank"] == t["last_rank"])
+    # add 3: the three remaining last-front points with the smallest add keys
+    rest = sorted(np.setdiff1d(L, Q).tolist(), key=lambda i: _oneshot_key(seed, gen, i, 1))
+    s_add, _ = oracle.nsga3_select(F, R, nP + nE0 + 3, seed, gen, mode=oracle.NICHE_ONESHOT)
+    assert np.array_equal(s_add, np.sort(np.concatenate([P, Q, rest[:3]])))
+    # drop 3: the three taken points with the smallest drop keys
+    taken = sorted(Q.tolist(), key=lambda i: _oneshot_key(seed, gen, i, 2))
+    s_drop, _ = oracle.nsga3_select(F, R, nP + nE0 - 3, seed, gen, mode=oracle.NICHE_ONESHOT)
+    assert np.array_equal(s_drop, np.sort(np.concatenate([P, taken[3:]])))
+    # exactly N survivors, P kept, picks from the last front only
+    for n_keep, sv in ((nP + nE0 + 3, s_add), (nP + nE0 - 3, s_drop)):
+        assert len(sv) == n_keep and np.all(np.isin(P, sv)) and np.all(np.isin(np.setdiff1d(sv, P), L))
