@@ -148,6 +148,31 @@ def triangle_tile_bytes(n2: int) -> int:
     return (nrb * ncb - 32 * (s * (s - 1) // 2) - t * s) * 4096
 
 
+def oneshot_timing(emo, torch, Ft, Rt, n_keep, seed, ws, flush, stream, steps):
+    """The same selection with the one-shot niche selection (Algorithm S.4 +
+    Update-Rank), device time per call (CUDA events, L2 flushed before each)."""
+    surv = torch.empty(n_keep, dtype=torch.int32, device=Ft.device)
+    for g in range(2):
+        emo.emo_nsga3_select(Ft, Rt, n_keep, seed, g, survivors=surv, ws=ws, niche_mode=emo.EMO_NICHE_ONESHOT)
+    emo.emo_set_stage_timing(True)
+    ms, niche = [], []
+    for k in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        emo.emo_nsga3_select(Ft, Rt, n_keep, seed, 2 + k, survivors=surv, ws=ws, niche_mode=emo.EMO_NICHE_ONESHOT)
+        b.record(stream)
+        niche.append(dict(emo.emo_stage_times()).get("niche", float("nan")))
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    emo.emo_set_stage_timing(False)
+    if emo.emo_workspace_status(ws) != 0:
+        raise SystemExit("one-shot selection failed on the device")
+    t = statistics.mean(ms)
+    return {"niche_mode": "one-shot (Algorithm S.4 + Update-Rank)", "steps": steps, "ms_per_step": t,
+            "selections_per_s": 1e3 / t, "niche_ms": statistics.mean(niche)}
+
+
 def batched_vs_plain(emo, torch, dev, rounds: int = 5):
     """64 uneven populations: one batched call replayed from a CUDA graph
     versus 64 plain calls on one stream (device time, CUDA events)."""
@@ -368,6 +393,8 @@ def main():
         "info": dict(zip(("status", "last_rank", "n_before", "n_last", "fallback_used", "n_recheck",
                           "n_fronts", "n_levels"), info_h)),
     }
+    if rank == 0 and world == 1:
+        line["oneshot"] = oneshot_timing(emo, torch, Ft, Rt, n_keep, seed, ws, flush, stream, max(3, args.steps // 2))
     if rank == 0 and world == 1 and not args.no_batch:
         line["batched_vs_plain"] = batched_vs_plain(emo, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -85,6 +85,8 @@ typedef struct {
     int32_t n_r;
     uint64_t seed;
     uint64_t generation;
+    int32_t niche_mode;    /* EMO_NICHE_EXACT (0) or EMO_NICHE_ONESHOT; zero-initialise */
+    int32_t reserved;      /* 0 */
 } emo_problem;
 
 typedef enum { EMO_OP_DOMINANCE = 0, EMO_OP_ND_RANK = 1, EMO_OP_NSGA3_SELECT = 2 } emo_op;
@@ -143,6 +145,28 @@ emo_status emo_nd_rank(const float* F, int64_t n2, int32_t m, int64_t n_keep, in
 emo_status emo_nsga3_select(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
                             int64_t n_keep, uint64_t seed, uint64_t generation, int32_t* survivors,
                             emo_select_info* info, void* ws, size_t ws_bytes, emo_stream_t stream);
+
+/* Niche selection of the last front. */
+#define EMO_NICHE_EXACT 0   /* Algorithm S.1: least-crowded references served level by level */
+#define EMO_NICHE_ONESHOT 1 /* the tensorized one-shot niche selection of Algorithm S.4 followed
+                               by Update-Rank (Algorithm S.6): every reference with niche count 0
+                               and last-front candidates takes its nearest candidate; then the
+                               remaining slots are filled from the other last-front points, or
+                               the surplus is dropped from the taken ones, in the order of Philox
+                               keys (counter (i, 0xFFFFFFF0 + tag, generation); tag 1 fills, tag 2
+                               drops) where the paper relies on a shuffled input. */
+
+/*
+ * emo_nsga3_select with the niche selection chosen by `niche_mode`
+ * (EMO_NICHE_EXACT or EMO_NICHE_ONESHOT; anything else gives
+ * EMO_ERR_INVALID_ARG) and the optional intermediates of `dbg` (a host
+ * pointer to a struct of device pointers, nullable). Steps a0-a8 are shared
+ * by both modes; other arguments as for emo_nsga3_select.
+ */
+emo_status emo_nsga3_select_ex(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
+                               int64_t n_keep, uint64_t seed, uint64_t generation, int32_t niche_mode,
+                               int32_t* survivors, emo_select_info* info, const emo_select_debug* dbg,
+                               void* ws, size_t ws_bytes, emo_stream_t stream);
 
 /* As emo_nsga3_select, also writing the intermediates named in `dbg` (a
  * host pointer to a struct of device pointers, nullable). */

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "EMO_OK", 1: "EMO_ERR_INVALID_ARG", 2: "EMO_ERR_NONFINITE", 3
                 4: "EMO_ERR_CUDA", 5: "EMO_ERR_TIMEOUT", 6: "EMO_ERR_NOT_IMPLEMENTED"}
 EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT = 0, 1, 2
 EMO_NOT_RANKED = 2147483647
+EMO_NICHE_EXACT, EMO_NICHE_ONESHOT = 0, 1
 EMO_MAX_BATCH = 128
 
 _lock = threading.Lock()
@@ -51,7 +52,7 @@ class Problem(ctypes.Structure):
     _fields_ = [("F", ctypes.c_void_p), ("R", ctypes.c_void_p), ("survivors", ctypes.c_void_p),
                 ("info", ctypes.c_void_p), ("n2", ctypes.c_int64), ("n_keep", ctypes.c_int64),
                 ("m", ctypes.c_int32), ("n_r", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("generation", ctypes.c_uint64)]
+                ("generation", ctypes.c_uint64), ("niche_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -81,6 +82,9 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             L.emo_nd_rank.argtypes = [vp, i64, i32, i64, vp, vp, vp, sz, vp]
             L.emo_nsga3_select.restype = ctypes.c_int
             L.emo_nsga3_select.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp, vp, sz, vp]
+            L.emo_nsga3_select_ex.restype = ctypes.c_int
+            L.emo_nsga3_select_ex.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, i32, vp, vp,
+                                              ctypes.POINTER(SelectDebug), vp, sz, vp]
             L.emo_nsga3_select_debug.restype = ctypes.c_int
             L.emo_nsga3_select_debug.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp,
                                                  ctypes.POINTER(SelectDebug), vp, sz, vp]
@@ -172,11 +176,14 @@ def emo_nd_rank(F: torch.Tensor, n_keep: int = 0, rank: torch.Tensor | None = No
 
 def emo_nsga3_select(F: torch.Tensor, R: torch.Tensor, n_keep: int, seed: int = 0, generation: int = 0,
                      survivors: torch.Tensor | None = None, info: torch.Tensor | None = None,
-                     ws: torch.Tensor | None = None, debug: dict | None = None, stream=None):
+                     ws: torch.Tensor | None = None, debug: dict | None = None, stream=None,
+                     niche_mode: int = 0):
     """Survivor indices (ascending, int32 ``[n_keep]``) on the device.
 
     ``info`` is an int32 tensor of 8 elements (``SelectInfo`` layout);
-    ``debug`` maps names of ``SelectDebug`` fields to device tensors.
+    ``debug`` maps names of ``SelectDebug`` fields to device tensors;
+    ``niche_mode`` is EMO_NICHE_EXACT (0) or EMO_NICHE_ONESHOT (1), which
+    goes through emo_nsga3_select_ex.
     """
     n2, m = F.shape
     n_r = R.shape[0]
@@ -188,7 +195,14 @@ def emo_nsga3_select(F: torch.Tensor, R: torch.Tensor, n_keep: int, seed: int = 
     ws = _ws(nbytes, ws, F.device)
     seed &= 0xFFFFFFFFFFFFFFFF
     generation &= 0xFFFFFFFFFFFFFFFF
-    if debug:
+    if niche_mode != EMO_NICHE_EXACT:
+        dbg = SelectDebug()
+        for k, t in (debug or {}).items():
+            setattr(dbg, k, _ptr(t))
+        rc = lib().emo_nsga3_select_ex(_ptr(F), n2, m, _ptr(R), n_r, n_keep, seed, generation, int(niche_mode),
+                                       _ptr(survivors), _ptr(info), ctypes.byref(dbg) if debug else None,
+                                       _ptr(ws), nbytes, _stream(stream))
+    elif debug:
         dbg = SelectDebug()
         for k, t in debug.items():
             setattr(dbg, k, _ptr(t))
@@ -215,6 +229,7 @@ def _problems(problems) -> ctypes.Array:
         arr[i].n_keep = p["n_keep"]
         arr[i].seed = p.get("seed", 0) & 0xFFFFFFFFFFFFFFFF
         arr[i].generation = p.get("generation", 0) & 0xFFFFFFFFFFFFFFFF
+        arr[i].niche_mode = int(p.get("niche_mode", EMO_NICHE_EXACT))
     return arr
 
 
@@ -224,7 +239,7 @@ def emo_batch_workspace_size(problems) -> int:
 
 
 def emo_nsga3_select_batch(problems, ws: torch.Tensor | None = None, stream=None):
-    """``problems``: list of dicts with F, R, n_keep, survivors[, info, seed, generation]."""
+    """``problems``: list of dicts with F, R, n_keep, survivors[, info, seed, generation, niche_mode]."""
     arr = _problems(problems)
     nbytes = int(lib().emo_batch_workspace_size(arr, len(problems)))
     if nbytes == 0:

@@ -96,9 +96,10 @@ DevInfo dev_info()
             return DevInfo{};
         int occ = 2;
         // k_peel takes peel_smem_bytes(ncb) of dynamic shared memory, the others none
-        const void* kernels[] = {(const void*)k_sort, (const void*)k_peel, (const void*)k_stats,
-                                 (const void*)k_csr, (const void*)k_niche, (const void*)k_finish};
-        const int dyn[] = {0, kPeelDynSmem, 0, 0, 0, 0};
+        const void* kernels[] = {(const void*)k_sort, (const void*)k_peel,  (const void*)k_stats,
+                                 (const void*)k_csr,  (const void*)k_niche, (const void*)k_niche_oneshot,
+                                 (const void*)k_finish};
+        const int dyn[] = {0, kPeelDynSmem, 0, 0, 0, 0, 0};
         for (int i = 0; i < (int)(sizeof(dyn) / sizeof(dyn[0])); ++i) {
             int o = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernels[i], kCoopThreads, dyn[i]) != cudaSuccess)
@@ -211,7 +212,13 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
         sm.mark("rescan");
         if (coop((const void*)k_csr, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
         sm.mark("csr");
-        if (coop((const void*)k_niche, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        bool any_exact = false, any_oneshot = false;
+        for (const ProbIn& in : ins) {
+            any_exact |= in.mode == MODE_SELECT && in.niche == EMO_NICHE_EXACT;
+            any_oneshot |= in.mode == MODE_SELECT && in.niche == EMO_NICHE_ONESHOT;
+        }
+        if (any_exact && coop((const void*)k_niche, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        if (any_oneshot && coop((const void*)k_niche_oneshot, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
         sm.mark("niche");
     }
     if (coop((const void*)k_finish, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
@@ -280,16 +287,27 @@ emo_status emo_nd_rank(const float* F, int64_t n2, int32_t m, int64_t n_keep, in
     return run(ins, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+emo_status emo_nsga3_select_ex(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
+                               int64_t n_keep, uint64_t seed, uint64_t generation, int32_t niche_mode,
+                               int32_t* survivors, emo_select_info* info, const emo_select_debug* dbg, void* ws,
+                               size_t ws_bytes, emo_stream_t stream)
+{
+    emo_status st = check_select_args(F, n2, m, R, n_r, n_keep, survivors);
+    if (st != EMO_OK) return st;
+    if (niche_mode != EMO_NICHE_EXACT && niche_mode != EMO_NICHE_ONESHOT) return EMO_ERR_INVALID_ARG;
+    std::vector<ProbIn> ins(1, make_in(F, R, n2, m, n_r, n_keep, seed, generation, survivors, info, MODE_SELECT));
+    ins[0].niche = niche_mode;
+    if (dbg) ins[0].dbg = *dbg;
+    return run(ins, ws, ws_bytes, (cudaStream_t)stream);
+}
+
 emo_status emo_nsga3_select_debug(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
                                   int64_t n_keep, uint64_t seed, uint64_t generation, int32_t* survivors,
                                   emo_select_info* info, const emo_select_debug* dbg, void* ws, size_t ws_bytes,
                                   emo_stream_t stream)
 {
-    emo_status st = check_select_args(F, n2, m, R, n_r, n_keep, survivors);
-    if (st != EMO_OK) return st;
-    std::vector<ProbIn> ins(1, make_in(F, R, n2, m, n_r, n_keep, seed, generation, survivors, info, MODE_SELECT));
-    if (dbg) ins[0].dbg = *dbg;
-    return run(ins, ws, ws_bytes, (cudaStream_t)stream);
+    return emo_nsga3_select_ex(F, n2, m, R, n_r, n_keep, seed, generation, EMO_NICHE_EXACT, survivors, info, dbg,
+                               ws, ws_bytes, stream);
 }
 
 emo_status emo_nsga3_select(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r, int64_t n_keep,
@@ -307,8 +325,10 @@ static bool batch_order(const emo_problem* descs, int32_t batch, std::vector<Pro
     for (int b = 0; b < batch; ++b) {
         const emo_problem& p = descs[b];
         if (check_select_args(p.F, p.n2, p.m, p.R, p.n_r, p.n_keep, p.survivors) != EMO_OK) return false;
+        if (p.niche_mode != EMO_NICHE_EXACT && p.niche_mode != EMO_NICHE_ONESHOT) return false;
         ins.push_back(make_in(p.F, p.R, p.n2, p.m, p.n_r, p.n_keep, p.seed, p.generation, p.survivors, p.info,
                               MODE_SELECT));
+        ins.back().niche = p.niche_mode;
     }
     std::stable_sort(ins.begin(), ins.end(), [](const ProbIn& a, const ProbIn& b) {
         return a.m != b.m ? a.m < b.m : a.n2 > b.n2;
@@ -380,7 +400,8 @@ int32_t emo_device_report(char* buf, int32_t len)
     struct K { const char* name; const void* fn; int dyn; };
     const K ks[] = {{"k_sort", (const void*)k_sort, 0}, {"k_peel", (const void*)k_peel, kPeelDynSmem},
                     {"k_stats", (const void*)k_stats, 0}, {"k_csr", (const void*)k_csr, 0},
-                    {"k_niche", (const void*)k_niche, 0}, {"k_finish", (const void*)k_finish, 0}};
+                    {"k_niche", (const void*)k_niche, 0}, {"k_niche_oneshot", (const void*)k_niche_oneshot, 0},
+                    {"k_finish", (const void*)k_finish, 0}};
     for (const K& k : ks) {
         cudaFuncAttributes fa{};
         int occ = -1;

@@ -57,7 +57,7 @@ struct ProbIn {
     uint64_t seed;
     uint64_t gen;
     int32_t mode;
-    int32_t pad_;
+    int32_t niche;           // EMO_NICHE_EXACT or EMO_NICHE_ONESHOT (MODE_SELECT)
     int32_t* rank_out;       // MODE_RANK
     int32_t* last_rank_out;  // nullable
     emo_select_debug dbg;
@@ -89,7 +89,7 @@ struct Scal {
     unsigned int bar_count;
     unsigned int bar_gen;
     int32_t ncol;            // niching: keys collected from the selected histogram bin
-    int32_t pad_[1];
+    int32_t nsel;            // one-shot niching: references that took their nearest candidate
 };
 
 // Device-side descriptor with every workspace pointer of one problem.
@@ -124,7 +124,7 @@ struct ProbDev {
     int32_t* loff;           // [n_r + 1] CSR offsets of the candidate lists
     int32_t* llist;          // [2][n2] last-front members (CSR order after sorting)
     int32_t* fen;            // [n2] Fenwick trees over each candidate list
-    unsigned long long* ekeys;  // [n_r] priorities of the references in a level
+    unsigned long long* ekeys;  // [max(n_r, n2)] niching keys collected from one histogram bin
     int32_t* nhist;          // niching: [kNicheBins] key histogram | [G] packed per-CTA (min, count)
     int32_t* elist;          // [n_r] references served in a level
     int32_t* flag;           // [n2] survivor flags / scan scratch
@@ -234,7 +234,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         o_loff = take((nr + 1) * 4);
         o_llist = take(2 * n2 * 4);
         o_fen = take(n2 * 4);
-        o_ekeys = take(nr * 8);
+        o_ekeys = take((nr > n2 ? nr : n2) * 8);
         o_elist = take(nr * 4);
         o_rord = take(2 * nr * 4);
         o_rphi = take(nr * 4);

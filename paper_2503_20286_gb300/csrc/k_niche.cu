@@ -100,23 +100,138 @@ __device__ __forceinline__ void fen_remove(int32_t* fen, int n, int slot)
     for (int x = slot + 1; x <= n; x += x & -x) fen[x - 1] -= 1;
 }
 
+// ------------------------------------------------------------ threshold select
+// The key of rank k (0-based) among the distinct 64-bit keys that the CTAs of
+// a group emit, computed by every CTA of the group: a histogram of the top 12
+// bits, the bin holding rank k, the keys of that bin collected in d.ekeys, and
+// the rank inside the bin (ranked in shared memory, or by a byte-wise radix
+// select when the bin is large). The caller clears `hist` and sc->ncol and
+// passes a group barrier before the call. for_keys(f) calls f(key) for each
+// key of the calling thread's share.
+constexpr int kNicheSmallSel = 2048;  // collected keys ranked in shared memory
+
+struct NicheSmem {
+    int warp[33];
+    unsigned long long keys[kNicheSmallSel];
+    int hist[kRadix];
+    unsigned long long prefix, thresh;
+    int k, bin, kbin;
+};
+
+template <class ForKeys>
+__device__ bool group_kth_key(const ProbDev& d, const Group& g, long long budget, int k, ForKeys for_keys,
+                              NicheSmem& sm, unsigned long long& thresh)
+{
+    Scal* sc = d.sc;
+    int32_t* hist = d.nhist;
+    const int tid = threadIdx.x;
+    for_keys([&](unsigned long long key) { atomicAdd(&hist[key >> 52], 1); });
+    if (!group_sync(sc, g.size, budget)) return false;
+
+    {  // the bin of the key of rank k (each thread scans 8 bins)
+        constexpr int PER = kNicheBins / kCoopThreads;
+        int h[PER], v = 0;
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            h[e] = __ldcg(&hist[tid * PER + e]);
+            v += h[e];
+        }
+        int tot;
+        int pre = block_exclusive_scan<kCoopThreads>(v, sm.warp, tot);
+        if (pre <= k && k < pre + v) {
+#pragma unroll
+            for (int e = 0; e < PER; ++e) {
+                if (k < pre + h[e]) {
+                    sm.bin = tid * PER + e;
+                    sm.kbin = k - pre;
+                    break;
+                }
+                pre += h[e];
+            }
+        }
+        __syncthreads();
+    }
+    const int bin = sm.bin, kbin = sm.kbin;
+    for_keys([&](unsigned long long key) {
+        if ((int)(key >> 52) == bin) d.ekeys[atomicAdd(&sc->ncol, 1)] = key;
+    });
+    if (!group_sync(sc, g.size, budget)) return false;
+
+    const int nc = ld_volatile(&sc->ncol);  // the rank-kbin key among the collected ones
+    if (nc <= kNicheSmallSel) {
+        for (int i = tid; i < nc; i += blockDim.x) sm.keys[i] = __ldcg(&d.ekeys[i]);
+        __syncthreads();
+        for (int i = tid; i < nc; i += blockDim.x) {
+            const unsigned long long key = sm.keys[i];
+            int r = 0;
+            for (int q = 0; q < nc; ++q) r += sm.keys[q] < key ? 1 : 0;
+            if (r == kbin) sm.thresh = key;
+        }
+        __syncthreads();
+    } else {  // many keys in one bin: byte-wise radix select
+        if (tid == 0) {
+            sm.prefix = 0ull;
+            sm.k = kbin;
+        }
+        unsigned long long mask = 0ull;
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            for (int i = tid; i < kRadix; i += blockDim.x) sm.hist[i] = 0;
+            __syncthreads();
+            const unsigned long long prefix = sm.prefix;
+            for (int e = tid; e < nc; e += blockDim.x) {
+                const unsigned long long key = __ldcg(&d.ekeys[e]);
+                if ((key & mask) == prefix) atomicAdd(&sm.hist[(key >> shift) & 0xFF], 1);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int acc = 0, dg = 0;
+                for (; dg < kRadix; ++dg) {
+                    if (acc + sm.hist[dg] > sm.k) break;
+                    acc += sm.hist[dg];
+                }
+                sm.k -= acc;
+                sm.prefix = prefix | ((unsigned long long)dg << shift);
+            }
+            mask |= 0xFFull << shift;
+            __syncthreads();
+        }
+        if (tid == 0) sm.thresh = sm.prefix;
+        __syncthreads();
+    }
+    thresh = sm.thresh;
+    __syncthreads();
+    return true;
+}
+
+// Nearest member of reference j's candidate list (d, then index).
+__device__ __forceinline__ int niche_nearest(const ProbDev& d, const int32_t* L, int off, int full)
+{
+    int pos = 0;
+    double bd = d.d64[L[off]];
+    int bi = L[off];
+    for (int t = 1; t < full; ++t) {
+        const int v = L[off + t];
+        const double dv = d.d64[v];
+        if (dv < bd || (dv == bd && v < bi)) {
+            bd = dv;
+            bi = v;
+            pos = t;
+        }
+    }
+    return pos;
+}
+
 // ------------------------------------------------------------ k_niche
 // One cooperative launch; the references of a problem are spread over its CTA
 // group, and a reference's list, Fenwick tree and counts are touched by one
 // thread only. Per level:
 //   (A) every CTA: the minimum niche count over its live references and how
-//       many hold it; the histogram of (C) is cleared;
+//       many hold it; the histogram of the threshold select is cleared;
 //   (B) every CTA: the group's minimum c and its count from the partials; if
-//       the level cannot be served in full, the histogram of the top 12 bits
-//       of the level's priorities (x0, j);
-//   (C) every CTA: the bin holding the `remaining`-th smallest priority; the
-//       keys of that bin are collected;
-//   (D) every CTA: the threshold (that priority, selected from the collected
-//       keys) and the picks of its references.
-// Every phase ends with a bounded group barrier; levels served in full skip
-// (B)'s histogram and (C).
-constexpr int kNicheSmallSel = 2048;  // collected keys ranked in shared memory
-
+//       the level cannot be served in full, the priority (x0, j) of rank
+//       remaining - 1 among the level's references (group_kth_key);
+//   (C) every CTA: the picks of its references.
+// Every phase ends with a bounded group barrier.
 __device__ __forceinline__ unsigned long long niche_key(uint64_t seed, uint64_t gen, int64_t j, int c)
 {
     return ((unsigned long long)niche_random(seed, gen, (uint32_t)j, (uint32_t)c, 0u) << 32) | (unsigned)j;
@@ -124,16 +239,12 @@ __device__ __forceinline__ unsigned long long niche_key(uint64_t seed, uint64_t 
 
 __global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
 {
-    __shared__ int s_warp[33];
-    __shared__ unsigned long long s_keys[kNicheSmallSel];
-    __shared__ int s_hist[kRadix];
-    __shared__ unsigned long long s_prefix, s_thresh;
-    __shared__ int s_k, s_bin, s_kbin;
+    __shared__ NicheSmem sm;
     const Group g = group_of(plan);
     const ProbDev& d = plan->p[g.prob];
     const ProbIn& in = d.in;
     const long long budget = plan->spin_budget;
-    if (in.mode != MODE_SELECT || ld_volatile(&d.sc->status) != 0) return;
+    if (in.mode != MODE_SELECT || in.niche != EMO_NICHE_EXACT || ld_volatile(&d.sc->status) != 0) return;
     Scal* sc = d.sc;
     const int tid = threadIdx.x;
     const int nr = in.n_r;
@@ -166,8 +277,8 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
                 }
             }
         }
-        const int bmin = block_reduce_min<kCoopThreads>(cmin, s_warp);
-        const int bcnt = block_reduce_sum<kCoopThreads>(cmin == bmin ? cnt : 0, s_warp);
+        const int bmin = block_reduce_min<kCoopThreads>(cmin, sm.warp);
+        const int bcnt = block_reduce_sum<kCoopThreads>(cmin == bmin ? cnt : 0, sm.warp);
         if (tid == 0) part[g.rank] = ((unsigned long long)(unsigned)bmin << 32) | (unsigned)bcnt;
         for (int64_t b = t0; b < kNicheBins; b += stride) hist[b] = 0;
         if (g.rank == 0 && tid == 0) sc->ncol = 0;
@@ -176,7 +287,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
         // (B) the level: minimum c over the group and the number of references holding it
         int lm = INT32_MAX;
         for (int r = tid; r < g.size; r += blockDim.x) lm = min(lm, (int)(__ldcg(&part[r]) >> 32));
-        const int c = block_reduce_min<kCoopThreads>(lm, s_warp);
+        const int c = block_reduce_min<kCoopThreads>(lm, sm.warp);
         if (c == INT32_MAX) {  // no live reference although picks remain
             if (g.rank == 0 && tid == 0) set_status(sc, EMO_ERR_INVALID_ARG);
             return;
@@ -186,115 +297,26 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
             const unsigned long long v = __ldcg(&part[r]);
             if ((int)(v >> 32) == c) lc += (int)(v & 0xFFFFFFFFull);
         }
-        const int ne = block_reduce_sum<kCoopThreads>(lc, s_warp);
+        const int ne = block_reduce_sum<kCoopThreads>(lc, sm.warp);
         const bool all = ne <= remaining;
         unsigned long long thresh = ~0ull;
-        if (!all) {
-            // priorities of the level's references; keep the `remaining` smallest
-            for (int64_t j = t0; j < nr; j += stride)
-                if (__ldcg(&d.lcnt[j]) > 0 && __ldcg(&d.rho[j]) == c)
-                    atomicAdd(&hist[niche_key(seed, gen, j, c) >> 52], 1);
-            if (!group_sync(sc, g.size, budget)) return;
-
-            // (C) the bin of the priority of rank remaining - 1 (each thread scans 8 bins)
-            {
-                constexpr int PER = kNicheBins / kCoopThreads;
-                int h[PER], v = 0;
-#pragma unroll
-                for (int e = 0; e < PER; ++e) {
-                    h[e] = __ldcg(&hist[tid * PER + e]);
-                    v += h[e];
-                }
-                int tot;
-                int pre = block_exclusive_scan<kCoopThreads>(v, s_warp, tot);
-                const int k = remaining - 1;
-                if (pre <= k && k < pre + v) {
-#pragma unroll
-                    for (int e = 0; e < PER; ++e) {
-                        if (k < pre + h[e]) {
-                            s_bin = tid * PER + e;
-                            s_kbin = k - pre;
-                            break;
-                        }
-                        pre += h[e];
-                    }
-                }
-                __syncthreads();
-            }
-            const int bin = s_bin, kbin = s_kbin;
-            for (int64_t j = t0; j < nr; j += stride)
-                if (__ldcg(&d.lcnt[j]) > 0 && __ldcg(&d.rho[j]) == c) {
-                    const unsigned long long key = niche_key(seed, gen, j, c);
-                    if ((int)(key >> 52) == bin) d.ekeys[atomicAdd(&sc->ncol, 1)] = key;
-                }
-            if (!group_sync(sc, g.size, budget)) return;
-
-            // (D) the kbin-th smallest collected key (keys are distinct: j is in the low bits)
-            const int nc = ld_volatile(&sc->ncol);
-            if (nc <= kNicheSmallSel) {
-                for (int i = tid; i < nc; i += blockDim.x) s_keys[i] = __ldcg(&d.ekeys[i]);
-                __syncthreads();
-                for (int i = tid; i < nc; i += blockDim.x) {
-                    const unsigned long long key = s_keys[i];
-                    int r = 0;
-                    for (int q = 0; q < nc; ++q) r += s_keys[q] < key ? 1 : 0;
-                    if (r == kbin) s_thresh = key;
-                }
-                __syncthreads();
-            } else {  // many keys in one bin: byte-wise radix select
-                if (tid == 0) {
-                    s_prefix = 0ull;
-                    s_k = kbin;
-                }
-                unsigned long long mask = 0ull;
-                for (int shift = 56; shift >= 0; shift -= 8) {
-                    for (int i = tid; i < kRadix; i += blockDim.x) s_hist[i] = 0;
-                    __syncthreads();
-                    const unsigned long long prefix = s_prefix;
-                    for (int e = tid; e < nc; e += blockDim.x) {
-                        const unsigned long long key = __ldcg(&d.ekeys[e]);
-                        if ((key & mask) == prefix) atomicAdd(&s_hist[(key >> shift) & 0xFF], 1);
-                    }
-                    __syncthreads();
-                    if (tid == 0) {
-                        int acc = 0, dg = 0;
-                        for (; dg < kRadix; ++dg) {
-                            if (acc + s_hist[dg] > s_k) break;
-                            acc += s_hist[dg];
-                        }
-                        s_k -= acc;
-                        s_prefix = prefix | ((unsigned long long)dg << shift);
-                    }
-                    mask |= 0xFFull << shift;
-                    __syncthreads();
-                }
-                if (tid == 0) s_thresh = s_prefix;
-                __syncthreads();
-            }
-            thresh = s_thresh;
+        if (!all) {  // keep the `remaining` references with the smallest priorities
+            auto level_keys = [&](auto&& f) {
+                for (int64_t j = t0; j < nr; j += stride)
+                    if (__ldcg(&d.lcnt[j]) > 0 && __ldcg(&d.rho[j]) == c) f(niche_key(seed, gen, j, c));
+            };
+            if (!group_kth_key(d, g, budget, remaining - 1, level_keys, sm, thresh)) return;
         }
 
-        // picks: every level reference (all) or those with priority <= thresh
+        // (C) picks: every level reference (all) or those with priority <= thresh
         for (int64_t j = t0; j < nr; j += stride) {
             const int len = d.lcnt[j];
             if (len <= 0 || d.rho[j] != c) continue;
             if (!all && niche_key(seed, gen, j, c) > thresh) continue;
             const int off = d.loff[j], full = d.loff[j + 1] - off;
             int pos;
-            if (c == 0) {
-                // nearest member; the list is untouched at level 0
-                pos = 0;
-                double bd = d.d64[L[off]];
-                int bi = L[off];
-                for (int t = 1; t < full; ++t) {
-                    const int v = L[off + t];
-                    const double dv = d.d64[v];
-                    if (dv < bd || (dv == bd && v < bi)) {
-                        bd = dv;
-                        bi = v;
-                        pos = t;
-                    }
-                }
+            if (c == 0) {  // nearest member; the list is untouched at level 0
+                pos = niche_nearest(d, L, off, full);
             } else {
                 const uint32_t u = niche_random(seed, gen, (uint32_t)j, (uint32_t)c, 1u);
                 const int rank = (int)(((unsigned long long)u * (unsigned long long)len) >> 32);
@@ -310,6 +332,79 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
         ++levels;
     }
     if (g.rank == 0 && tid == 0) sc->levels = levels;
+}
+
+// ------------------------------------------------------------ k_niche_oneshot
+// The tensorized one-shot niche selection (Algorithm S.4) with Update-Rank
+// (Algorithm S.6), as one cooperative launch over the problem's CTA group:
+//   (A) every reference with niche count 0 and at least one last-front
+//       candidate takes its nearest candidate (d, then index); the taken
+//       points are counted (n_sel); the select histogram is cleared;
+//   (B) n_dif = K - n_sel. n_dif > 0: the n_dif remaining last-front points
+//       with the smallest add keys are added; n_dif < 0: the -n_dif taken
+//       points with the smallest drop keys are dropped. The keys, Philox x0 of
+//       counter (i, 0xFFFFFFF0 + tag, generation) with the index below, stand
+//       for the paper's shuffled input order.
+__device__ __forceinline__ unsigned long long oneshot_key(uint64_t seed, uint64_t gen, int64_t i, uint32_t tag)
+{
+    const uint4 ctr = make_uint4((uint32_t)i, 0xFFFFFFF0u + tag, (uint32_t)gen, (uint32_t)(gen >> 32));
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    return ((unsigned long long)philox4x32_10(ctr, key).x << 32) | (unsigned)i;
+}
+
+__global__ void __launch_bounds__(kCoopThreads, 1) k_niche_oneshot(Plan* plan)
+{
+    __shared__ NicheSmem sm;
+    const Group g = group_of(plan);
+    const ProbDev& d = plan->p[g.prob];
+    const ProbIn& in = d.in;
+    const long long budget = plan->spin_budget;
+    if (in.mode != MODE_SELECT || in.niche != EMO_NICHE_ONESHOT || ld_volatile(&d.sc->status) != 0) return;
+    Scal* sc = d.sc;
+    const int tid = threadIdx.x;
+    const int nr = in.n_r;
+    const int nP = ld_volatile(&sc->nP), nL = ld_volatile(&sc->nL);
+    const int K = (int)(in.n_keep - nP);
+    const int32_t* L = d.llist + (int64_t)ld_volatile(&sc->lbuf) * in.n2;
+    const uint64_t seed = in.seed, gen = in.gen;
+    const int64_t t0 = (int64_t)g.rank * blockDim.x + tid;
+    const int64_t stride = (int64_t)g.size * blockDim.x;
+
+    // (A) nearest candidate of every empty niche
+    int taken = 0;
+    for (int64_t j = t0; j < nr; j += stride) {
+        const int len = d.lcnt[j];
+        if (len <= 0 || d.rho[j] != 0) continue;
+        const int off = d.loff[j];
+        d.flag[L[off + niche_nearest(d, L, off, len)]] = 1;
+        ++taken;
+    }
+    taken = block_reduce_sum<kCoopThreads>(taken, sm.warp);
+    if (tid == 0 && taken) atomicAdd(&sc->nsel, taken);
+    for (int64_t b = t0; b < kNicheBins; b += stride) d.nhist[b] = 0;
+    if (g.rank == 0 && tid == 0) {
+        sc->ncol = 0;
+        sc->levels = 1;
+    }
+    if (!group_sync(sc, g.size, budget)) return;
+
+    // (B) Update-Rank: add or drop in Philox order
+    const int n_dif = K - ld_volatile(&sc->nsel);
+    if (n_dif == 0) return;
+    const uint32_t tag = n_dif > 0 ? 1u : 2u;
+    const int want = n_dif > 0 ? 0 : 1;  // add from the untaken points, drop from the taken ones
+    auto keys = [&](auto&& f) {
+        for (int64_t t = t0; t < nL; t += stride) {
+            const int i = __ldcg(&L[t]);
+            if (__ldcg(&d.flag[i]) == want) f(oneshot_key(seed, gen, i, tag));
+        }
+    };
+    unsigned long long thresh;
+    if (!group_kth_key(d, g, budget, (n_dif > 0 ? n_dif : -n_dif) - 1, keys, sm, thresh)) return;
+    for (int64_t t = t0; t < nL; t += stride) {
+        const int i = __ldcg(&L[t]);
+        if (__ldcg(&d.flag[i]) == want && oneshot_key(seed, gen, i, tag) <= thresh) d.flag[i] = 1 - want;
+    }
 }
 
 // ------------------------------------------------------------ k_finish

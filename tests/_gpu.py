@@ -9,7 +9,7 @@ from paper_2503_20286_gb300 import _binding as emo
 DEBUG_FIELDS = ("rank", "z", "extreme", "a", "fnorm", "pi", "dist", "rho", "picked")
 
 
-def gpu_select(F, R, n_keep, seed, gen=0, debug=True):
+def gpu_select(F, R, n_keep, seed, gen=0, debug=True, mode=0):
     dev = torch.device("cuda")
     Ft = torch.from_numpy(np.ascontiguousarray(F, np.float32)).to(dev)
     Rt = torch.from_numpy(np.ascontiguousarray(R, np.float32)).to(dev)
@@ -27,7 +27,7 @@ def gpu_select(F, R, n_keep, seed, gen=0, debug=True):
                "dist": torch.empty(n2, dtype=torch.float64, device=dev),
                "rho": torch.empty(n_r, dtype=torch.int32, device=dev),
                "picked": torch.empty(n2, dtype=torch.uint8, device=dev)}
-    surv = emo.emo_nsga3_select(Ft, Rt, n_keep, seed, gen, info=info, debug=dbg)
+    surv = emo.emo_nsga3_select(Ft, Rt, n_keep, seed, gen, info=info, debug=dbg, niche_mode=mode)
     torch.cuda.synchronize()
     inf = dict(zip(("status", "last_rank", "n_before", "n_last", "fallback_used", "n_recheck", "n_fronts",
                     "n_levels"), info.cpu().tolist()))
@@ -37,10 +37,11 @@ def gpu_select(F, R, n_keep, seed, gen=0, debug=True):
     return surv.cpu().numpy(), inf, out
 
 
-def compare_select(F, R, n_keep, seed, gen=0, check_debug=True):
-    """Bit-exact survivors and intermediates against the oracle."""
-    s_or, t = oracle.nsga3_select(F, R, n_keep, seed, gen)
-    s_gpu, info, g = gpu_select(F, R, n_keep, seed, gen, debug=check_debug)
+def compare_select(F, R, n_keep, seed, gen=0, check_debug=True, mode=0):
+    """Bit-exact survivors and intermediates against the oracle (niche mode
+    0: Algorithm S.1 levels, 1: one-shot Algorithm S.4 + S.6)."""
+    s_or, t = oracle.nsga3_select(F, R, n_keep, seed, gen, mode=mode)
+    s_gpu, info, g = gpu_select(F, R, n_keep, seed, gen, debug=check_debug, mode=mode)
     assert info["status"] == 0, info
     assert info["last_rank"] == t["last_rank"]
     assert info["n_before"] == t["n_before"] and info["n_last"] == t["n_last"]
