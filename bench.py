@@ -122,12 +122,12 @@ class ClockSampler:
 
 # DRAM traffic of k_dom_pref<3> per byte of stored tiles, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum of one launch at
-# 2N=100,000, M=3: 15.80 MB read + 575.10 MB written for 635.79 MB of tiles).
+# 2N=100,000, M=3: 15.80 MB read + 575.21 MB written for 635.79 MB of tiles).
 # The kernel's reads (prefix sets, keys) and writes (tiles) grow with the tiles
 # it writes, so the bench scales it by the timed workload's tile bytes. It is
 # reported only while the kernel sources are the ones it was measured on.
-DOM_TRAFFIC_PER_TILE_BYTE = (15_796_224 + 575_102_208) / 635_785_216
-DOM_TRAFFIC_SOURCES_SHA1 = "d4df74551b0e70501a88b24ac14513551d154490"
+DOM_TRAFFIC_PER_TILE_BYTE = (15_799_552 + 575_214_080) / 635_785_216
+DOM_TRAFFIC_SOURCES_SHA1 = "fe263295d35cc681b4d7212dbd3f78cdfe274f93"
 DOM_SOURCES = ("k_dominance.cu", "emo_kernels.cuh", "emo_internal.cuh")
 
 
@@ -139,6 +139,21 @@ def dom_sources_sha1() -> str:
                   "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def peel_read_bytes(emo, torch, Ft, F, n_keep: int) -> int:
+    """Bytes the peel must read: every row of the fronts peeled before the last
+    one (rank < l) is read once, 128 bytes per column block at or right of
+    the row's block in lexicographic order (ranks from emo_nd_rank)."""
+    rank, last = emo.emo_nd_rank(Ft, n_keep)
+    torch.cuda.synchronize()
+    r = rank.cpu().numpy()
+    l = int(last.cpu().numpy().reshape(-1)[0])
+    order = np.lexsort(tuple(F[:, k] for k in range(F.shape[1] - 1, -1, -1)))
+    pos = np.empty(F.shape[0], dtype=np.int64)
+    pos[order] = np.arange(F.shape[0])
+    ncb = -(-F.shape[0] // 1024)
+    return int(128 * np.sum(ncb - pos[r < l] // 1024))
 
 
 def triangle_tile_bytes(n2: int) -> int:
@@ -368,6 +383,12 @@ def main():
     # tiles; achieved = tile bytes / kernel time against measured HBM copy BW
     tile_bytes = triangle_tile_bytes(n2)
     achieved = tile_bytes / (dom_ms / 1e3) / 1e9
+    # peel roofline: the rows of the fronts before the last, read once from HBM
+    peel_ms = statistics.mean(stage_ms.get("peel", [float("nan")]))
+    peel_bytes = peel_read_bytes(emo, torch, Ft, F, n_keep)
+    peel_roofline = {"bound": "hbm", "kernel": "k_peel", "achieved": peel_bytes / (peel_ms / 1e3) / 1e9,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": peel_bytes / (peel_ms / 1e3) / 1e9 / pk["hbm_gbs"], "algorithmic_bytes": peel_bytes}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -386,6 +407,7 @@ def main():
                      "traffic_source": "ncu dram bytes at 2N=100k scaled by tile bytes",
                      "algorithmic_bytes": tile_bytes,
                      "peak_source": f"{pk['source']} HBM copy bandwidth"},
+        "peel_roofline": peel_roofline,
         "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(F.nbytes + R.nbytes), "d2h_bytes_per_step": int(n_keep * 4)},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
