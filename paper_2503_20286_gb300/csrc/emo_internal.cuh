@@ -90,6 +90,8 @@ struct Scal {
     unsigned int bar_gen;
     int32_t ncol;            // niching: keys collected from the selected histogram bin
     int32_t nsel;            // one-shot niching: references that took their nearest candidate
+    int32_t longrun;         // sort: a run of equal f_1 longer than the in-place fix-up handles
+    int32_t pad2_;
 };
 
 // Device-side descriptor with every workspace pointer of one problem.

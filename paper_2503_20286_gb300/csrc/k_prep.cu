@@ -117,15 +117,70 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
     const float* F = in.F;
     __shared__ RadixSmem rsm;
 
+    // Lexicographic order of (f_1, ..., f_m), ties by index. First a stable
+    // radix sort by f_1; then every run of equal f_1 (almost always short for
+    // continuous objectives) is put in (f_2, ..., f_m, index) order in place
+    // by one thread. If some run is longer than kShortRun, the full stable
+    // LSD sort over all objectives runs instead (from the index order).
     int buf = 0;
-    for (int k = m - 1; k >= 0; --k) {
+    auto sort_by = [&](int k) -> bool {
         for (int shift = 0; shift < 32; shift += kRadixBits) {
             const int32_t* src = d.idx + (int64_t)buf * d.n2p;
             int32_t* dst = d.idx + (int64_t)(buf ^ 1) * d.n2p;
             bool skipped = false;
             auto key = [&](int32_t v) { return float_key(__ldg(&F[(int64_t)v * m + k])); };
-            if (!radix_pass(d, g, gs, budget, n2, src, dst, shift, key, skipped, rsm)) return;
+            if (!radix_pass(d, g, gs, budget, n2, src, dst, shift, key, skipped, rsm)) return false;
             if (!skipped) buf ^= 1;
+        }
+        return true;
+    };
+    if (!sort_by(0)) return;
+    {
+        constexpr int kShortRun = 32;
+        int32_t* cur = d.idx + (int64_t)buf * d.n2p;
+        auto key0 = [&](int64_t s) { return float_key(__ldg(&F[(int64_t)__ldcg(&cur[s]) * m])); };
+        // (f_2, ..., f_m, index) order of two points
+        auto before = [&](int32_t a, int32_t b) {
+            for (int k = 1; k < m; ++k) {
+                const uint32_t ka = float_key(__ldg(&F[(int64_t)a * m + k]));
+                const uint32_t kb = float_key(__ldg(&F[(int64_t)b * m + k]));
+                if (ka != kb) return ka < kb;
+            }
+            return a < b;
+        };
+        // a run's f_1 is the same at every one of its positions, so the
+        // neighbours' reads below see the same keys while other threads
+        // permute their own runs
+        const int64_t stride = (int64_t)g.size * blockDim.x;
+        for (int64_t s = (int64_t)g.rank * blockDim.x + threadIdx.x; s + 1 < n2; s += stride) {
+            const uint32_t k0 = key0(s);
+            if ((s > 0 && key0(s - 1) == k0) || key0(s + 1) != k0) continue;  // not the start of a run
+            int64_t e = s + 2;
+            while (e < n2 && e - s <= kShortRun && key0(e) == k0) ++e;
+            if (e - s > kShortRun) {
+                d.sc->longrun = 1;
+                continue;
+            }
+            for (int64_t i = s + 1; i < e; ++i) {  // insertion sort, stable (reads bypass L1)
+                const int32_t v = __ldcg(&cur[i]);
+                int64_t j = i;
+                while (j > s) {
+                    const int32_t u = __ldcg(&cur[j - 1]);
+                    if (!before(v, u)) break;
+                    cur[j] = u;
+                    --j;
+                }
+                cur[j] = v;
+            }
+        }
+        if (!group_sync(d.sc, g.size, budget)) return;
+        if (ld_volatile(&d.sc->longrun)) {  // full stable LSD sort from the index order
+            int32_t* id = d.idx + (int64_t)(buf ^ 1) * d.n2p;
+            for (int64_t s = (int64_t)g.rank * blockDim.x + threadIdx.x; s < n2; s += stride) id[s] = (int32_t)s;
+            buf ^= 1;
+            if (!group_sync(d.sc, g.size, budget)) return;
+            for (int k = m - 1; k >= 0; --k)
+                if (!sort_by(k)) return;
         }
     }
     if (g.rank == 0 && threadIdx.x == 0) d.sc->idx_buf = buf;

@@ -135,6 +135,19 @@ def test_select_exactly_filled_fronts():
     assert t["last_rank"] == 4 and t["n_before"] + t["n_last"] == n_keep
 
 
+@pytest.mark.parametrize("run", [3, 40])
+def test_select_ties_in_the_first_objective(run):
+    # f_1 takes each value `run` times (runs of equal f_1 in the sorted
+    # order): short runs are ordered in place, a run longer than 32 makes the
+    # sort fall back to the full radix sort over every objective
+    F = wl.population(3000, 3, 9, "sphere", seed=31)
+    order = np.argsort(F[:, 0], kind="stable")
+    F[order, 0] = (np.arange(3000) // run).astype(np.float32) / np.float32(1024)
+    _gpu.compare_select(F, wl.das_dennis(30, 3), 1400, seed=5)
+    r, _ = _gpu.gpu_rank(F)
+    assert np.array_equal(r, oracle.nd_sort_deb(F))
+
+
 def test_select_all_duplicates():
     F = np.tile(np.array([[0.25, 0.5, 0.125]], dtype=np.float32), (700, 1))
     _gpu.compare_select(F, wl.das_dennis(6, 3), 300, seed=3)
