@@ -63,13 +63,16 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_csr(Plan* plan)
     const int32_t* L = d.llist + (int64_t)buf * n2;
     if (g.rank == 0 && threadIdx.x == 0) sc->lbuf = buf;
 
-    // CSR offsets from the run boundaries of the sorted list
-    for (int64_t t = t0; t < nL; t += stride) {
-        const int j = __ldcg(&d.pi[__ldcg(&L[t])]);
-        const int jp = t > 0 ? __ldcg(&d.pi[__ldcg(&L[t - 1])]) : -1;
-        for (int q = jp + 1; q <= j; ++q) d.loff[q] = (int32_t)t;
-        if (t == nL - 1)
-            for (int q = j + 1; q <= nr; ++q) d.loff[q] = nL;
+    // CSR offsets: loff[q] = first position of the sorted list whose point is
+    // associated with a reference >= q (one binary search per reference)
+    for (int64_t q = t0; q <= nr; q += stride) {
+        int lo = 0, hi = nL;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldcg(&d.pi[__ldcg(&L[mid])]) < q) lo = mid + 1;
+            else hi = mid;
+        }
+        d.loff[q] = lo;
     }
     if (!group_sync(sc, g.size, budget)) return;
     for (int64_t t = t0; t < nL; t += stride) {
