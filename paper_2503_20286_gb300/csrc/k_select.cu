@@ -15,6 +15,7 @@
 //     rigorous error band of the best are re-evaluated with the FP64
 //     perpendicular distance d^2 = sum (f_k - t r_k)^2, t = f.r / r.r.
 #include "emo_kernels.cuh"
+#include "group_radix.cuh"
 
 namespace emo {
 
@@ -225,6 +226,35 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_stats(Plan* plan)
         }
         sc->fallback = fallback;
         __threadfence();
+    }
+
+    // 6. S in the order of the polar angle of its normalised points (16-bit
+    // buckets, two radix passes): neighbouring threads of the association
+    // then scan neighbouring references. Any order of S gives the same result.
+    if (!group_sync(sc, g.size, budget)) return;
+    __shared__ RadixSmem rsm;
+    float zf[kMaxM], ia[kMaxM];
+    for (int k = 0; k < m; ++k) {
+        zf[k] = __ldcg(&sc->z[k]);
+        ia[k] = __ldcg(&sc->inv_a32[k]);
+    }
+    auto akey = [&](int32_t v) {
+        float f[kMaxM];
+        for (int k = 0; k < m; ++k) f[k] = (F[(int64_t)v * m + k] - zf[k]) * ia[k];
+        const int b = (int)(polar_angle(f, m) * (65535.0f / 1.5707964f));
+        return (uint32_t)(b < 0 ? 0 : (b > 65535 ? 65535 : b));
+    };
+    int32_t* bufs[2] = {d.slist, d.llist};
+    int cur = 0;
+    const int gsS = (int)max((int64_t)1, min((int64_t)g.size, cdiv(nS, 4096)));
+    for (int shift = 0; shift < 16; shift += kRadixBits) {
+        bool skipped = false;
+        if (!radix_pass(d, g, gsS, budget, nS, bufs[cur], bufs[cur ^ 1], shift, akey, skipped, rsm)) return;
+        if (!skipped) cur ^= 1;
+    }
+    if (cur == 1) {
+        for (int64_t i = t0; i < nS; i += stride) d.slist[i] = __ldcg(&d.llist[i]);
+        group_sync(sc, g.size, budget);
     }
 }
 
