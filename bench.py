@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "dominance pairs/s and selections/s at 2N=400k; batched vs plain; % of roofline"
 UNIT = "pairs/s"
 N2, M, H, D_VARS = 400_000, 3, 631, 12
-SAMPLE_N2, SAMPLE_H = 16_000, 126        # oracle sample: first 16,000 points, 8,128 directions
+SAMPLE_N2, SAMPLE_H = 40_000, 199        # oracle sample: first 40,000 points, 20,100 directions (about 10 s)
 FLUSH_BYTES = 512 << 20                   # > 129 MB L2
 KERNELS_PER_STEP = 12                     # launches of one single-population selection
 
