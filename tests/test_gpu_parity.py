@@ -181,6 +181,10 @@ def test_select_same_seed_same_survivors_other_generation_differs():
     a, _, _ = _gpu.gpu_select(F, R, 2000, seed=11, gen=1, debug=False)
     b, _, _ = _gpu.gpu_select(F, R, 2000, seed=11, gen=1, debug=False)
     assert np.array_equal(a, b)
+    # the random niching choices are keyed by the generation
+    c, _, _ = _gpu.gpu_select(F, R, 2000, seed=11, gen=2, debug=False)
+    assert np.array_equal(c, oracle.nsga3_select(F, R, 2000, 11, 2)[0])
+    assert not np.array_equal(a, c)
 
 
 def test_select_config1_full_size():
