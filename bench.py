@@ -286,6 +286,7 @@ def main():
     import torch.distributed as dist
     from paper_2503_20286_gb300 import build as emo_build
     from paper_2503_20286_gb300 import _binding as emo
+    from paper_2503_20286_gb300.replicas import max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -343,11 +344,7 @@ def main():
     clk = clocks.stop()
     emo.emo_set_stage_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)  # the whole job waits for the slowest rank
     st = emo.emo_workspace_status(ws)
     if st != 0:
         raise SystemExit(f"selection failed on the device: status {st}")
@@ -368,11 +365,7 @@ def main():
         S_host.copy_(surv, non_blocking=True)
     e_e.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e_s.elapsed_time(e_e) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e_s.elapsed_time(e_e) / e2e_steps, dev)
 
     pairs = float(n2) * float(n2)
     ms_per_step = total_ms / args.steps
