@@ -398,6 +398,11 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
         const int rb_lo = chunk * kDomRowChunk, rb_hi = min(rbmax, rb_lo + kDomRowChunk);
         const int dupcut = d.minrs[cb];
         const int64_t cbase = (int64_t)cb * kColBlock;
+        // in registers: the tile stores could alias the plan, which would
+        // otherwise reload these after every row block
+        uint32_t* const Dm = d.D;
+        const float* const keys = d.keys;
+        const int ncb = d.ncb;
         VCount<kDomNH> vlo, vhi;
 
         // keys of the lane's row in the warp's next row block (prefetched)
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
         {
             const int64_t pl = (int64_t)(rb_lo + warp) * kTileRows + lane;
 #pragma unroll
-            for (int k = 0; k < K; ++k) key[k] = (rb_lo + warp < rb_hi && pl < n2) ? __ldg(&d.keys[pl * K + k]) : 0.0f;
+            for (int k = 0; k < K; ++k) key[k] = (rb_lo + warp < rb_hi && pl < n2) ? __ldg(&keys[pl * K + k]) : 0.0f;
         }
         for (int rb = rb_lo + warp; rb < rb_hi; rb += NW) {
             const int64_t pl = (int64_t)rb * kTileRows + lane;
@@ -416,12 +421,12 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
                 const int rbn = rb + NW;
                 const int64_t pn = (int64_t)rbn * kTileRows + lane;
 #pragma unroll
-                for (int k = 0; k < K; ++k) key[k] = (rbn < rb_hi && pn < n2) ? __ldg(&d.keys[pn * K + k]) : 0.0f;
+                for (int k = 0; k < K; ++k) key[k] = (rbn < rb_hi && pn < n2) ? __ldg(&keys[pn * K + k]) : 0.0f;
             }
             const bool diag = (int64_t)rb * kTileRows + 31 >= cbase;
             const bool dup = rb * kTileRows + 31 >= dupcut;
             const int64_t rowbase = (int64_t)rb * kTileRows;
-            uint32_t* tile = d.D + tile_index(rb, cb, d.ncb) * (int64_t)(kTileRows * kTileWords);
+            uint32_t* tile = Dm + tile_index(rb, cb, ncb) * (int64_t)(kTileRows * kTileWords);
             if (dup) pref_rows<K, true, true>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
             else if (diag) pref_rows<K, true, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
             else pref_rows<K, false, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
@@ -474,15 +479,18 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
         const int rb_lo = chunk * kDomRowChunk, rb_hi = min(rbmax, rb_lo + kDomRowChunk);
         const int dupcut = d.minrs[cb];
         const int64_t cbase = (int64_t)cb * kColBlock;
+        uint32_t* const Dm = d.D;
+        const float* const keys = d.keys;
+        const int ncb = d.ncb;
         VCount<kDomNH> vlo, vhi;
         for (int rb = rb_lo + warp; rb < rb_hi; rb += NW) {
             const int64_t pl = (int64_t)rb * kTileRows + lane;
             for (int k = 0; k < K; ++k)
-                myst[k * 32 + lane] = pl < n2 ? count_ge_halves(obj + k * G.obj_bytes, __ldg(&d.keys[pl * K + k])) : 0;
+                myst[k * 32 + lane] = pl < n2 ? count_ge_halves(obj + k * G.obj_bytes, __ldg(&keys[pl * K + k])) : 0;
             __syncwarp();
             const bool diag = (int64_t)rb * kTileRows + 31 >= cbase;
             const bool dup = rb * kTileRows + 31 >= dupcut;
-            uint32_t* tile = d.D + tile_index(rb, cb, d.ncb) * (int64_t)(kTileRows * kTileWords);
+            uint32_t* tile = Dm + tile_index(rb, cb, ncb) * (int64_t)(kTileRows * kTileWords);
             unsigned long long* dst = reinterpret_cast<unsigned long long*>(tile + h * 16 * 32) + l;
 #pragma unroll 1
             for (int g = 0; g < 2; ++g) {

@@ -124,6 +124,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n2 = in.n2, n2p = d.n2p;
     const int ncb = d.ncb;
+    // workspace pointers in registers: the copy asm clobbers memory, which
+    // would otherwise reload them from the plan before every copy
+    const uint32_t* const Dm = d.D;
+    int32_t* const cntp = d.cnt;
+    int32_t* const rank_s = d.rank_s;
     uint32_t* ring = reinterpret_cast<uint32_t*>(s_dyn) + warp * (kPeelStages * 32 * 32);
     int* s_pref = s_dyn + kPeelRingBytes / 4;
     int* s_mem = s_pref + ncb + 1;
@@ -137,10 +142,10 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
         __syncthreads();
         for (int q = tid; q < kColBlock; q += blockDim.x) {
             const int64_t s = (int64_t)cb * kColBlock + q;
-            if (s < n2 && __ldcg(&d.cnt[s]) == 0) {
+            if (s < n2 && __ldcg(&cntp[s]) == 0) {
                 const int slot = atomicAdd(&s_newn, 1);
                 d.front[(int64_t)cb * kColBlock + slot] = peel_encode(s, ncb);
-                d.rank_s[s] = 0;
+                rank_s[s] = 0;
             }
         }
         __syncthreads();
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
 #pragma unroll
                 for (int u = 0; u < kColBlock / kCoopThreads; ++u) {
                     const int64_t sq = (int64_t)cb * kColBlock + tid + u * kCoopThreads;
-                    cpre[u] = sq < n2 ? __ldcg(&d.cnt[sq]) : 0;
+                    cpre[u] = sq < n2 ? __ldcg(&cntp[sq]) : 0;
                 }
                 __syncthreads();
                 VCount<kPeelNH> vc;
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                         if (b < nb && i < nmem) {
                             const uint32_t e = (uint32_t)s_mem[i];
                             const int64_t t = (int64_t)(e >> 5) + cb;
-                            cp_async16(smem_u32(dst + j * 32 + q * 4), d.D + (t << 10) + ((e & 31u) << 5) + q * 4);
+                            cp_async16(smem_u32(dst + j * 32 + q * 4), Dm + (t << 10) + ((e & 31u) << 5) + q * 4);
                         }
                     }
                     cp_async_commit();
@@ -261,11 +266,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                     const int64_t s = (int64_t)cb * kColBlock + q;
                     if (dq && s < n2) {
                         const int c = cpre[u] - dq;
-                        d.cnt[s] = c;
+                        cntp[s] = c;
                         if (c == 0) {
                             const int slot = atomicAdd(&s_newn, 1);
                             fw[(int64_t)cb * kColBlock + slot] = peel_encode(s, ncb);
-                            d.rank_s[s] = k + 1;
+                            rank_s[s] = k + 1;
                         }
                     }
                 }
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
         int r = kNotRanked;
         int32_t v = 0;
         if (s < n2) {
-            r = __ldcg(&d.rank_s[s]);
+            r = __ldcg(&rank_s[s]);
             v = __ldcg(&idx[s]);
             d.rank_o[v] = r;
             if (in.mode == MODE_RANK && in.rank_out) in.rank_out[v] = r;
