@@ -62,6 +62,10 @@ def lib():
                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32,
                 ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
                 ctypes.POINTER(_Trace)]
+            _lib.oracle_hype_select.restype = ctypes.c_int
+            _lib.oracle_hype_select.argtypes = [
+                ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             _lib.oracle_nsga3_select_mode.restype = ctypes.c_int
             _lib.oracle_nsga3_select_mode.argtypes = [
                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32,
@@ -170,3 +174,20 @@ def nsga3_select(F, R, n_keep: int, seed: int, generation: int = 0, trace: bool 
     for k in ("last_rank", "n_before", "n_last", "fallback", "n_levels", "near_ties"):
         out[k] = int(getattr(t, k))
     return surv, out
+
+
+def hype_select(F, v_ref, U, n_keep: int):
+    """TensorHypE selection (Algorithms S.10, S.11): survivors (ascending),
+    the estimated hypervolume contribution of every point and l. ``U`` holds
+    the s x m uniform [0, 1) numbers of the Monte Carlo samples."""
+    F = _f32(F)
+    v_ref = _f32(v_ref).reshape(-1)
+    U = _f32(U)
+    n2, m = F.shape
+    surv = np.zeros(n_keep, dtype=np.int32)
+    vhv = np.zeros(n2, dtype=np.float64)
+    last = np.zeros(1, dtype=np.int32)
+    rc = lib().oracle_hype_select(_p(F), n2, m, _p(v_ref), _p(U), U.shape[0], n_keep, _p(surv), _p(vhv), _p(last))
+    if rc != 0:
+        raise OracleError(f"oracle_hype_select status {rc}")
+    return surv, vhv, int(last[0])

@@ -580,3 +580,120 @@ int oracle_nsga3_select(const float* F, int64_t n2, int m, const float* R, int32
 {
     return oracle_nsga3_select_mode(F, n2, m, R, n_r, n_keep, seed, gen, 0, survivors, tr);
 }
+
+/* ---------------------------------------------------------------------- */
+/* TensorHypE environmental selection (Algorithm S.10) with the Monte      */
+/* Carlo hypervolume estimation of Algorithm S.11.                          */
+/*   - r, l: Algorithm S.2 ranks, l = rank of the n-th best point;          */
+/*     the mask H(l - r) keeps S = {r <= l}, k = |S| - n points to drop.     */
+/*   - lambda_1 = 1, lambda_i = (k - (i - 1)) / (n1 - (i - 1)) (i >= 2),     */
+/*     alpha_c = (lambda_1 ... lambda_c) / c, n1 = 2N (all points); the     */
+/*     product reaches 0 at c = k + 1, so alpha_c = 0 beyond k.             */
+/*   - samples S_i = f_l + U_i (v_ref - f_l) with f_l = min_i F_i, in float */
+/*     (one subtraction, one multiply, one add, no fused multiply-add);     */
+/*     U (uniform [0,1) numbers) is an input.                               */
+/*   - t_pds(p, i) = 1 iff F_p <= S_i in every objective; c_i = sum_p.      */
+/*   - v_hv(p) = (sum over c ascending of alpha_c * h_p(c)) * vol / s, with */
+/*     h_p(c) = samples dominated by p whose c_i = c (equal to the sum of   */
+/*     alpha_{c_i} over p's samples, in a fixed order); vol = prod_j       */
+/*     (v_ref_j - f_l_j) in double.                                          */
+/*   - I = lexsort(r, -d)[:n]: every point with r < l, then the points of   */
+/*     front l by d descending (ties: lower index); output ascending.       */
+/* ---------------------------------------------------------------------- */
+int oracle_hype_select(const float* F, int64_t n2, int m, const float* vref, const float* U, int32_t s,
+                       int64_t n_keep, int32_t* survivors, double* vhv_out, int32_t* last_rank_out)
+{
+    if (!F || !vref || !U || !survivors || m < 2 || m > 16 || n2 < 1 || s < 1 || n_keep < 1 || n_keep > n2)
+        return ORACLE_EINVAL;
+    for (int64_t i = 0; i < n2 * m; ++i) if (!isfinite(F[i])) return ORACLE_ENONFINITE;
+    int status = ORACLE_ENOMEM;
+    int32_t* rank = (int32_t*)malloc((size_t)n2 * sizeof(int32_t));
+    int32_t* sorted = (int32_t*)malloc((size_t)n2 * sizeof(int32_t));
+    double* alpha = (double*)malloc((size_t)(n2 + 1) * sizeof(double));
+    float* S = (float*)malloc((size_t)s * (size_t)m * sizeof(float));
+    int64_t* c = (int64_t*)calloc((size_t)s, sizeof(int64_t));
+    int64_t* h = (int64_t*)calloc((size_t)(n2 + 1), sizeof(int64_t));
+    double* vhv = (double*)malloc((size_t)n2 * sizeof(double));
+    int64_t* order = (int64_t*)malloc((size_t)n2 * sizeof(int64_t));
+    if (!rank || !sorted || !alpha || !S || !c || !h || !vhv || !order) goto done_h;
+
+    if (oracle_nd_sort_deb(F, n2, m, rank) < 0) goto done_h;
+    memcpy(sorted, rank, (size_t)n2 * sizeof(int32_t));
+    qsort(sorted, (size_t)n2, sizeof(int32_t), cmp_i32);
+    int32_t l = sorted[n_keep - 1];
+    int64_t nS = 0, nP = 0;
+    for (int64_t i = 0; i < n2; ++i) { nS += rank[i] <= l; nP += rank[i] < l; }
+    int64_t k = nS - n_keep;
+
+    /* alpha_c, c = 1 .. n1 (alpha[0] unused) */
+    {
+        double prod = 1.0;                         /* lambda_1 = 1 */
+        alpha[0] = 0.0;
+        for (int64_t cc = 1; cc <= n2; ++cc) {
+            if (cc >= 2) prod = prod * ((double)(k - (cc - 1)) / (double)(n2 - (cc - 1)));
+            alpha[cc] = prod / (double)cc;
+        }
+    }
+    /* samples in [f_l, v_ref] */
+    float fl[16];
+    for (int j = 0; j < m; ++j) {
+        float mn = INFINITY;
+        for (int64_t i = 0; i < n2; ++i) if (F[i * m + j] < mn) mn = F[i * m + j];
+        fl[j] = mn;
+    }
+    for (int32_t i = 0; i < s; ++i)
+        for (int j = 0; j < m; ++j) {
+            volatile float width = vref[j] - fl[j];
+            volatile float step = U[(int64_t)i * m + j] * width;
+            S[(int64_t)i * m + j] = fl[j] + step;
+        }
+    /* c_i: points weakly dominating sample i */
+    for (int32_t i = 0; i < s; ++i)
+        for (int64_t p = 0; p < n2; ++p) {
+            int dom = 1;
+            for (int j = 0; j < m; ++j) if (!(F[p * m + j] <= S[(int64_t)i * m + j])) { dom = 0; break; }
+            c[i] += dom;
+        }
+    double vol = 1.0;
+    for (int j = 0; j < m; ++j) vol = vol * ((double)vref[j] - (double)fl[j]);
+    /* v_hv(p) over its dominated samples, grouped by their count */
+    for (int64_t p = 0; p < n2; ++p) {
+        int64_t cmax = 0;
+        for (int32_t i = 0; i < s; ++i) {
+            int dom = 1;
+            for (int j = 0; j < m; ++j) if (!(F[p * m + j] <= S[(int64_t)i * m + j])) { dom = 0; break; }
+            if (dom) { h[c[i]] += 1; if (c[i] > cmax) cmax = c[i]; }
+        }
+        double v = 0.0;
+        for (int64_t cc = 1; cc <= cmax; ++cc)
+            if (h[cc]) { v = v + alpha[cc] * (double)h[cc]; h[cc] = 0; }
+        vhv[p] = v * vol / (double)s;
+    }
+    /* I = lexsort(r, -d)[:n]: P, then front l by (d descending, index) */
+    int64_t nl = 0;
+    for (int64_t i = 0; i < n2; ++i) if (rank[i] == l) order[nl++] = i;
+    for (int64_t a = 1; a < nl; ++a) {           /* insertion sort, stable */
+        int64_t x = order[a], b = a;
+        while (b > 0) {
+            int64_t y = order[b - 1];
+            if (vhv[x] > vhv[y] || (vhv[x] == vhv[y] && x < y)) { order[b] = y; --b; } else break;
+        }
+        order[b] = x;
+    }
+    {
+        uint8_t* keep = (uint8_t*)calloc((size_t)n2, 1);
+        if (!keep) goto done_h;
+        for (int64_t i = 0; i < n2; ++i) keep[i] = rank[i] < l;
+        for (int64_t e = 0; e < n_keep - nP; ++e) keep[order[e]] = 1;
+        int64_t ns = 0;
+        for (int64_t i = 0; i < n2; ++i) if (keep[i]) survivors[ns++] = (int32_t)i;
+        free(keep);
+        status = ns == n_keep ? ORACLE_OK : ORACLE_EINVAL;
+    }
+    if (vhv_out) memcpy(vhv_out, vhv, (size_t)n2 * sizeof(double));
+    if (last_rank_out) *last_rank_out = l;
+
+done_h:
+    free(rank); free(sorted); free(alpha); free(S); free(c); free(h); free(vhv); free(order);
+    return status;
+}

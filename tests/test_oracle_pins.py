@@ -18,6 +18,10 @@ off-by-one in l, a wrong Philox constant, a wrong pivot rule...) fails here:
   orthogonal to R_j gives distance delta ||u||.
 * Niching equals a literal one-pick-at-a-time run of Algorithm S.1 that
   breaks ties by the same random priorities.
+* TensorHypE selection (Algorithms S.10, S.11): with k = 1 the estimate of
+  each point is its exclusive hypervolume, exact on a regular sample lattice;
+  with one front and N = 1 the estimates sum to sum_i (n1 - c_i)/(n1 - 1)
+  (c_i counted by brute force); P is kept, nothing beyond front l.
 * One-shot niching (Algorithm S.4 + Update-Rank, Algorithm S.6): when the
   number of empty niches with candidates equals K, it selects exactly what
   the level form selects at its only level (a separate code path); adding
@@ -395,3 +399,67 @@ def test_oneshot_add_and_drop_follow_philox_order(idx):
     # exactly N survivors, P kept, picks from the last front only
     for n_keep, sv in ((nP + nE0 + 3, s_add), (nP + nE0 - 3, s_drop)):
         assert len(sv) == n_keep and np.all(np.isin(P, sv)) and np.all(np.isin(np.setdiff1d(sv, P), L))
+
+
+def _lattice(g, m=2):
+    u = (np.arange(g, dtype=np.float64) + 0.5) / g
+    grid = np.stack(np.meshgrid(*([u] * m), indexing="ij"), axis=-1).reshape(-1, m)
+    return grid.astype(np.float32)
+
+
+def test_hype_exclusive_volume_on_a_lattice():
+    # three points of one front and one dominated point; f_l = (1, 1), v_ref = (4, 4)
+    F = np.array([[1, 3], [2, 2], [3, 1], [2, 3]], np.float32)
+    U = _lattice(30)                                   # samples 1.05, 1.15, ..., 3.95 per axis
+    surv, vhv, l = oracle.hype_select(F, np.array([4, 4], np.float32), U, 2)   # k = 1
+    assert l == 0
+    # each front point alone dominates a 1 x 1 square: 100 lattice samples of 900, volume 9
+    assert vhv[:3].tolist() == [1.0, 1.0, 1.0]
+    assert vhv[3] == 0.0                              # every sample it dominates has c >= 3
+    assert surv.tolist() == [0, 1]                    # equal estimates: lower indices kept
+
+
+def test_hype_drops_the_smallest_exclusive_volume():
+    # exclusive areas 0.5, 0.75 and 1.5; lattice samples 1.0375 + 0.075 i per
+    # axis: 7 x 13, 20 x 7 and 13 x 20 of them fall in those regions
+    F = np.array([[1, 3], [1.5, 2.5], [3, 1]], np.float32)
+    U = _lattice(40)
+    surv, vhv, _ = oracle.hype_select(F, np.array([4, 4], np.float32), U, 2)
+    assert vhv.tolist() == [91 * 9 / 1600, 140 * 9 / 1600, 260 * 9 / 1600]
+    assert surv.tolist() == [1, 2]
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_hype_weights_sum_identity(m):
+    rng = np.random.default_rng(31 + m)
+    F = wl.front_points(40, m, "linear", seed=60 + m)         # one front
+    v_ref = np.full(m, 0.7, np.float32)
+    U = rng.random((500, m)).astype(np.float32)
+    _, vhv, l = oracle.hype_select(F, v_ref, U, 1)            # k = n1 - 1
+    assert l == 0
+    n1 = F.shape[0]
+    fl = F.min(axis=0)
+    S = (fl + U * (v_ref - fl).astype(np.float32)).astype(np.float32)
+    c = (F[None, :, :] <= S[:, None, :]).all(axis=2).sum(axis=1)
+    vol = np.prod(v_ref.astype(np.float64) - fl.astype(np.float64))
+    expect = np.sum((n1 - c[c > 0]) / (n1 - 1)) * vol / U.shape[0]
+    assert abs(vhv.sum() - expect) <= 1e-12 * max(1.0, expect)
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_hype_selection_invariants(case):
+    rng = np.random.default_rng(80 + case)
+    m = int(rng.integers(2, 5))
+    n2 = int(rng.integers(30, 200))
+    F = wl.population(n2, m, m + 4, "sphere", seed=90 + case)
+    U = rng.random((300, m)).astype(np.float32)
+    n_keep = int(rng.integers(1, n2 + 1))
+    surv, vhv, l = oracle.hype_select(F, (F.max(axis=0) + 0.1).astype(np.float32), U, n_keep)
+    r = oracle.nd_sort_deb(F)
+    assert l == np.sort(r)[n_keep - 1]
+    assert len(surv) == n_keep and np.all(np.diff(surv) > 0)
+    assert np.all(np.isin(np.flatnonzero(r < l), surv)) and np.all(r[surv] <= l)
+    last = np.setdiff1d(np.flatnonzero(r == l), surv)
+    kept = np.setdiff1d(surv, np.flatnonzero(r < l))
+    if len(last) and len(kept):   # every kept last-front point scores at least every dropped one
+        assert vhv[kept].min() >= vhv[last].max()
