@@ -593,10 +593,8 @@ int oracle_nsga3_select(const float* F, int64_t n2, int m, const float* R, int32
 /*     (one subtraction, one multiply, one add, no fused multiply-add);     */
 /*     U (uniform [0,1) numbers) is an input.                               */
 /*   - t_pds(p, i) = 1 iff F_p <= S_i in every objective; c_i = sum_p.      */
-/*   - v_hv(p) = (sum over c ascending of alpha_c * h_p(c)) * vol / s, with */
-/*     h_p(c) = samples dominated by p whose c_i = c (equal to the sum of   */
-/*     alpha_{c_i} over p's samples, in a fixed order); vol = prod_j       */
-/*     (v_ref_j - f_l_j) in double.                                          */
+/*   - v_hv(p) = (sum of alpha_{c_i} over the samples i that p dominates,   */
+/*     i ascending) * vol / s; vol = prod_j (v_ref_j - f_l_j) in double.     */
 /*   - I = lexsort(r, -d)[:n]: every point with r < l, then the points of   */
 /*     front l by d descending (ties: lower index); output ascending.       */
 /* ---------------------------------------------------------------------- */
@@ -612,10 +610,9 @@ int oracle_hype_select(const float* F, int64_t n2, int m, const float* vref, con
     double* alpha = (double*)malloc((size_t)(n2 + 1) * sizeof(double));
     float* S = (float*)malloc((size_t)s * (size_t)m * sizeof(float));
     int64_t* c = (int64_t*)calloc((size_t)s, sizeof(int64_t));
-    int64_t* h = (int64_t*)calloc((size_t)(n2 + 1), sizeof(int64_t));
     double* vhv = (double*)malloc((size_t)n2 * sizeof(double));
     int64_t* order = (int64_t*)malloc((size_t)n2 * sizeof(int64_t));
-    if (!rank || !sorted || !alpha || !S || !c || !h || !vhv || !order) goto done_h;
+    if (!rank || !sorted || !alpha || !S || !c || !vhv || !order) goto done_h;
 
     if (oracle_nd_sort_deb(F, n2, m, rank) < 0) goto done_h;
     memcpy(sorted, rank, (size_t)n2 * sizeof(int32_t));
@@ -656,17 +653,14 @@ int oracle_hype_select(const float* F, int64_t n2, int m, const float* vref, con
         }
     double vol = 1.0;
     for (int j = 0; j < m; ++j) vol = vol * ((double)vref[j] - (double)fl[j]);
-    /* v_hv(p) over its dominated samples, grouped by their count */
+    /* v_hv(p): the weights of the samples p dominates, in sample order */
     for (int64_t p = 0; p < n2; ++p) {
-        int64_t cmax = 0;
+        double v = 0.0;
         for (int32_t i = 0; i < s; ++i) {
             int dom = 1;
             for (int j = 0; j < m; ++j) if (!(F[p * m + j] <= S[(int64_t)i * m + j])) { dom = 0; break; }
-            if (dom) { h[c[i]] += 1; if (c[i] > cmax) cmax = c[i]; }
+            if (dom) v = v + alpha[c[i]];
         }
-        double v = 0.0;
-        for (int64_t cc = 1; cc <= cmax; ++cc)
-            if (h[cc]) { v = v + alpha[cc] * (double)h[cc]; h[cc] = 0; }
         vhv[p] = v * vol / (double)s;
     }
     /* I = lexsort(r, -d)[:n]: P, then front l by (d descending, index) */
@@ -694,6 +688,6 @@ int oracle_hype_select(const float* F, int64_t n2, int m, const float* vref, con
     if (last_rank_out) *last_rank_out = l;
 
 done_h:
-    free(rank); free(sorted); free(alpha); free(S); free(c); free(h); free(vhv); free(order);
+    free(rank); free(sorted); free(alpha); free(S); free(c); free(vhv); free(order);
     return status;
 }
