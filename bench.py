@@ -188,6 +188,37 @@ def oneshot_timing(emo, torch, Ft, Rt, n_keep, seed, ws, flush, stream, steps):
             "selections_per_s": 1e3 / t, "niche_ms": statistics.mean(niche)}
 
 
+def hype_timing(emo, torch, Ft, F, n_keep, flush, stream, steps, n_samples: int = 10_000):
+    """TensorHypE selection (Algorithms S.10, S.11) of the same population
+    with n_samples Monte Carlo samples: device time per call (CUDA events,
+    L2 flushed before each)."""
+    U = np.random.Generator(np.random.Philox(7)).random((n_samples, F.shape[1])).astype(np.float32)
+    v_ref = (F.max(axis=0) * np.float32(1.1)).astype(np.float32)
+    Ut, vt = torch.from_numpy(U).to(Ft.device), torch.from_numpy(v_ref).to(Ft.device)
+    nbytes = emo.emo_workspace_size(emo.EMO_OP_HYPE_SELECT, F.shape[0], F.shape[1], n_samples)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=Ft.device)
+    surv = torch.empty(n_keep, dtype=torch.int32, device=Ft.device)
+    for _ in range(2):
+        emo.emo_hype_select(Ft, vt, Ut, n_keep, survivors=surv, ws=ws)
+    emo.emo_set_stage_timing(True)
+    ms, hype = [], []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        emo.emo_hype_select(Ft, vt, Ut, n_keep, survivors=surv, ws=ws)
+        b.record(stream)
+        hype.append(dict(emo.emo_stage_times()).get("hype", float("nan")))
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    emo.emo_set_stage_timing(False)
+    if emo.emo_workspace_status(ws) != 0:
+        raise SystemExit("HypE selection failed on the device")
+    t = statistics.mean(ms)
+    return {"selection": "TensorHypE (Algorithms S.10, S.11)", "samples": n_samples, "steps": steps,
+            "ms_per_step": t, "selections_per_s": 1e3 / t, "hype_stage_ms": statistics.mean(hype)}
+
+
 def batched_vs_plain(emo, torch, dev, rounds: int = 5):
     """64 uneven populations: one batched call replayed from a CUDA graph
     versus 64 plain calls on one stream (device time, CUDA events)."""
@@ -410,6 +441,8 @@ def main():
     }
     if rank == 0 and world == 1:
         line["oneshot"] = oneshot_timing(emo, torch, Ft, Rt, n_keep, seed, ws, flush, stream, max(3, args.steps // 2))
+        del ws  # the HypE workspace replaces it
+        line["hype"] = hype_timing(emo, torch, Ft, F, n_keep, flush, stream, max(3, args.steps // 2))
     if rank == 0 and world == 1 and not args.no_batch:
         line["batched_vs_plain"] = batched_vs_plain(emo, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -89,7 +89,7 @@ typedef struct {
     int32_t reserved;      /* 0 */
 } emo_problem;
 
-typedef enum { EMO_OP_DOMINANCE = 0, EMO_OP_ND_RANK = 1, EMO_OP_NSGA3_SELECT = 2 } emo_op;
+typedef enum { EMO_OP_DOMINANCE = 0, EMO_OP_ND_RANK = 1, EMO_OP_NSGA3_SELECT = 2, EMO_OP_HYPE_SELECT = 3 } emo_op;
 
 /* Bytes of workspace needed by `op` for a population of n2 points with m
  * objectives and n_r reference directions (n_r ignored for ranking). Returns
@@ -188,6 +188,33 @@ emo_status emo_nsga3_select_debug(const float* F, int64_t n2, int32_t m, const f
 size_t emo_batch_workspace_size(const emo_problem* descs, int32_t batch);
 emo_status emo_nsga3_select_batch(const emo_problem* descs, int32_t batch, void* ws,
                                   size_t ws_bytes, emo_stream_t stream);
+
+/*
+ * TensorHypE environmental selection (Algorithm S.10) with the Monte Carlo
+ * hypervolume estimation of Algorithm S.11: ranks and l as for
+ * emo_nsga3_select; k = |{rank <= l}| - n_keep; samples S_i = f_l + U_i
+ * (v_ref - f_l) (float, f_l = the column minima of F); c_i = the points
+ * weakly dominating S_i; a point's contribution = vol / s times the sum of
+ * alpha_{c_i} over the samples it dominates, in sample order, with
+ * alpha_c = (lambda_1 ... lambda_c) / c, lambda_1 = 1,
+ * lambda_i = (k - i + 1) / (n2 - i + 1) (zero beyond c = k); survivors =
+ * every point with rank < l plus the points of front l with the largest
+ * contributions (ties: lower index), ascending.
+ *   F          [n2*m] objectives (device), as for emo_nsga3_select.
+ *   v_ref      [m] reference point (device), finite.
+ *   U          [n_samples*m] uniform numbers in [0, 1) (device), the caller's
+ *              random draws of the samples.
+ *   n_samples  s >= 1.
+ *   survivors  [n_keep] int32 output, ascending.
+ *   info       device emo_select_info*, nullable (n_levels = 0).
+ *   hv         [n2] double output (device, nullable): the contribution of
+ *              each point of front l, 0 elsewhere.
+ *   ws         workspace of emo_workspace_size(EMO_OP_HYPE_SELECT, n2, m,
+ *              n_samples) bytes.
+ */
+emo_status emo_hype_select(const float* F, int64_t n2, int32_t m, const float* v_ref, const float* U,
+                           int32_t n_samples, int64_t n_keep, int32_t* survivors, emo_select_info* info,
+                           double* hv, void* ws, size_t ws_bytes, emo_stream_t stream);
 
 /*
  * emo_nsga3_select without a caller workspace, for callers that cannot

@@ -595,6 +595,8 @@ int oracle_nsga3_select(const float* F, int64_t n2, int m, const float* R, int32
 /*   - t_pds(p, i) = 1 iff F_p <= S_i in every objective; c_i = sum_p.      */
 /*   - v_hv(p) = (sum of alpha_{c_i} over the samples i that p dominates,   */
 /*     i ascending) * vol / s; vol = prod_j (v_ref_j - f_l_j) in double.     */
+/*     Only the points of front l are ordered by it, so it is reported for  */
+/*     them and 0 elsewhere; with k = 0 nothing is dropped and it is 0.     */
 /*   - I = lexsort(r, -d)[:n]: every point with r < l, then the points of   */
 /*     front l by d descending (ties: lower index); output ascending.       */
 /* ---------------------------------------------------------------------- */
@@ -656,6 +658,7 @@ int oracle_hype_select(const float* F, int64_t n2, int m, const float* vref, con
     /* v_hv(p): the weights of the samples p dominates, in sample order */
     for (int64_t p = 0; p < n2; ++p) {
         double v = 0.0;
+        if (rank[p] != l || k == 0) { vhv[p] = 0.0; continue; }
         for (int32_t i = 0; i < s; ++i) {
             int dom = 1;
             for (int j = 0; j < m; ++j) if (!(F[p * m + j] <= S[(int64_t)i * m + j])) { dom = 0; break; }

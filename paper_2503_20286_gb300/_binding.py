@@ -19,7 +19,7 @@ from . import build as _build
 EMO_OK = 0
 STATUS_NAMES = {0: "EMO_OK", 1: "EMO_ERR_INVALID_ARG", 2: "EMO_ERR_NONFINITE", 3: "EMO_ERR_WORKSPACE",
                 4: "EMO_ERR_CUDA", 5: "EMO_ERR_TIMEOUT", 6: "EMO_ERR_NOT_IMPLEMENTED"}
-EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT = 0, 1, 2
+EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT, EMO_OP_HYPE_SELECT = 0, 1, 2, 3
 EMO_NOT_RANKED = 2147483647
 EMO_NICHE_EXACT, EMO_NICHE_ONESHOT = 0, 1
 EMO_MAX_BATCH = 128
@@ -82,6 +82,8 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             L.emo_nd_rank.argtypes = [vp, i64, i32, i64, vp, vp, vp, sz, vp]
             L.emo_nsga3_select.restype = ctypes.c_int
             L.emo_nsga3_select.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp, vp, sz, vp]
+            L.emo_hype_select.restype = ctypes.c_int
+            L.emo_hype_select.argtypes = [vp, i64, i32, vp, vp, i32, i64, vp, vp, vp, vp, sz, vp]
             L.emo_nsga3_select_ex.restype = ctypes.c_int
             L.emo_nsga3_select_ex.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, i32, vp, vp,
                                               ctypes.POINTER(SelectDebug), vp, sz, vp]
@@ -213,6 +215,25 @@ def emo_nsga3_select(F: torch.Tensor, R: torch.Tensor, n_keep: int, seed: int = 
         rc = lib().emo_nsga3_select(_ptr(F), n2, m, _ptr(R), n_r, n_keep, seed, generation, _ptr(survivors),
                                     _ptr(info), _ptr(ws), nbytes, _stream(stream))
     _check(rc, "emo_nsga3_select")
+    return survivors
+
+
+def emo_hype_select(F: torch.Tensor, v_ref: torch.Tensor, U: torch.Tensor, n_keep: int,
+                    survivors: torch.Tensor | None = None, info: torch.Tensor | None = None,
+                    hv: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """TensorHypE selection: survivor indices (ascending, int32 ``[n_keep]``).
+    ``U`` holds the ``[s, m]`` uniform numbers of the Monte Carlo samples;
+    ``hv`` (float64 ``[n2]``, optional) receives the contributions of front l."""
+    n2, m = F.shape
+    ns = U.shape[0]
+    if survivors is None:
+        survivors = torch.empty(n_keep, dtype=torch.int32, device=F.device)
+    nbytes = emo_workspace_size(EMO_OP_HYPE_SELECT, n2, m, ns)
+    if nbytes == 0:
+        raise EmoError(1, "emo_workspace_size")
+    ws = _ws(nbytes, ws, F.device)
+    _check(lib().emo_hype_select(_ptr(F), n2, m, _ptr(v_ref), _ptr(U), ns, n_keep, _ptr(survivors), _ptr(info),
+                                 _ptr(hv), _ptr(ws), nbytes, _stream(stream)), "emo_hype_select")
     return survivors
 
 

@@ -98,8 +98,8 @@ DevInfo dev_info()
         // k_peel takes peel_smem_bytes(ncb) of dynamic shared memory, the others none
         const void* kernels[] = {(const void*)k_sort, (const void*)k_peel,  (const void*)k_stats,
                                  (const void*)k_csr,  (const void*)k_niche, (const void*)k_niche_oneshot,
-                                 (const void*)k_finish};
-        const int dyn[] = {0, kPeelDynSmem, 0, 0, 0, 0, 0};
+                                 (const void*)k_hype, (const void*)k_finish};
+        const int dyn[] = {0, kPeelDynSmem, 0, 0, 0, 0, 0, 0};
         for (int i = 0; i < (int)(sizeof(dyn) / sizeof(dyn[0])); ++i) {
             int o = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernels[i], kCoopThreads, dyn[i]) != cudaSuccess)
@@ -156,12 +156,13 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
     if (!ws || !aligned(ws, 256)) return EMO_ERR_INVALID_ARG;
     int64_t off = kPlanBytes;
     int max_ncb = 1;
-    bool any_select = false;
+    bool any_select = false, any_hype = false;
     for (auto& in : ins) {
         in.ws_off = (uint64_t)off;
         off += layout_problem(in, di.G, nullptr, nullptr);
         max_ncb = std::max<int>(max_ncb, (int)cdiv(in.n2, kColBlock));
         any_select |= in.mode == MODE_SELECT;
+        any_hype |= in.mode == MODE_HYPE;
     }
     if ((int64_t)ws_bytes < off) return EMO_ERR_WORKSPACE;
 
@@ -221,6 +222,10 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
         if (any_oneshot && coop((const void*)k_niche_oneshot, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
         sm.mark("niche");
     }
+    if (any_hype) {
+        if (coop((const void*)k_hype, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("hype");
+    }
     if (coop((const void*)k_finish, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("finish");
     return EMO_OK;
@@ -250,10 +255,13 @@ size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r)
 {
     if (!sizes_ok(n2, m)) return 0;
     if (op == EMO_OP_DOMINANCE) return 0;
-    int mode = op == EMO_OP_ND_RANK ? MODE_RANK : op == EMO_OP_NSGA3_SELECT ? MODE_SELECT : 0;
+    int mode = op == EMO_OP_ND_RANK ? MODE_RANK
+               : op == EMO_OP_NSGA3_SELECT ? MODE_SELECT
+               : op == EMO_OP_HYPE_SELECT ? MODE_HYPE
+                                          : 0;
     if (!mode) return 0;
-    if (mode == MODE_SELECT && n_r < 1) return 0;
-    ProbIn in = make_in(nullptr, nullptr, n2, m, mode == MODE_SELECT ? n_r : 1, n2, 0, 0, nullptr, nullptr, mode);
+    if ((mode == MODE_SELECT || mode == MODE_HYPE) && n_r < 1) return 0;
+    ProbIn in = make_in(nullptr, nullptr, n2, m, mode == MODE_RANK ? 1 : n_r, n2, 0, 0, nullptr, nullptr, mode);
     int64_t b = problem_bytes(in);
     return b < 0 ? 0 : (size_t)(kPlanBytes + b);
 }
@@ -284,6 +292,19 @@ emo_status emo_nd_rank(const float* F, int64_t n2, int32_t m, int64_t n_keep, in
     std::vector<ProbIn> ins(1, make_in(F, nullptr, n2, m, 1, n_keep, 0, 0, nullptr, nullptr, MODE_RANK));
     ins[0].rank_out = rank;
     ins[0].last_rank_out = last_rank;
+    return run(ins, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+emo_status emo_hype_select(const float* F, int64_t n2, int32_t m, const float* v_ref, const float* U,
+                           int32_t n_samples, int64_t n_keep, int32_t* survivors, emo_select_info* info,
+                           double* hv, void* ws, size_t ws_bytes, emo_stream_t stream)
+{
+    emo_status st = check_select_args(F, n2, m, v_ref, n_samples, n_keep, survivors);
+    if (st != EMO_OK) return st;
+    if (!U || !aligned(U, 4) || (hv && !aligned(hv, 8))) return EMO_ERR_INVALID_ARG;
+    std::vector<ProbIn> ins(1, make_in(F, v_ref, n2, m, n_samples, n_keep, 0, 0, survivors, info, MODE_HYPE));
+    ins[0].U = U;
+    ins[0].hv_out = hv;
     return run(ins, ws, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -401,6 +422,7 @@ int32_t emo_device_report(char* buf, int32_t len)
     const K ks[] = {{"k_sort", (const void*)k_sort, 0}, {"k_peel", (const void*)k_peel, kPeelDynSmem},
                     {"k_stats", (const void*)k_stats, 0}, {"k_csr", (const void*)k_csr, 0},
                     {"k_niche", (const void*)k_niche, 0}, {"k_niche_oneshot", (const void*)k_niche_oneshot, 0},
+                    {"k_hype", (const void*)k_hype, 0},
                     {"k_finish", (const void*)k_finish, 0}};
     for (const K& k : ks) {
         cudaFuncAttributes fa{};

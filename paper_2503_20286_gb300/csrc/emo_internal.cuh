@@ -42,7 +42,7 @@ constexpr int kRadix = 1 << kRadixBits;
 constexpr int64_t kMaxN2 = int64_t(1) << 21;
 constexpr int32_t kNotRanked = EMO_NOT_RANKED;
 
-enum Mode : int32_t { MODE_RANK = 1, MODE_SELECT = 2 };
+enum Mode : int32_t { MODE_RANK = 1, MODE_SELECT = 2, MODE_HYPE = 3 };
 
 // What the host knows about one problem.
 struct ProbIn {
@@ -58,6 +58,8 @@ struct ProbIn {
     uint64_t gen;
     int32_t mode;
     int32_t niche;           // EMO_NICHE_EXACT or EMO_NICHE_ONESHOT (MODE_SELECT)
+    const float* U;          // MODE_HYPE: [n_r * m] uniform numbers of the samples (n_r = samples; R = v_ref)
+    double* hv_out;          // MODE_HYPE: [n2] contributions of front l (nullable)
     int32_t* rank_out;       // MODE_RANK
     int32_t* last_rank_out;  // nullable
     emo_select_debug dbg;
@@ -205,7 +207,7 @@ __host__ __device__ constexpr int64_t colprep_obj_bytes(int K)
 // it on the device.
 __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char* base, ProbDev* d)
 {
-    const int64_t n2 = in.n2, m = in.m, nr = in.mode == MODE_SELECT ? in.n_r : 1;
+    const int64_t n2 = in.n2, m = in.m, nr = (in.mode == MODE_SELECT || in.mode == MODE_HYPE) ? in.n_r : 1;
     const int64_t nrb = cdiv(n2, 32), ncb = cdiv(n2, kColBlock), n2p = ncb * kColBlock;
     const int64_t ntiles = tiles_before(nrb, ncb);
     int64_t off = 0;
@@ -244,6 +246,14 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         o_rsort = take(nr * m * 4);
         o_fbound = take(n2 * 4);
         o_nhist = take(kNicheBins * 4 + int64_t(G) * 8);
+    } else if (in.mode == MODE_HYPE) {
+        // d64: contributions; rhat: samples; rho: their dominator counts;
+        // llist: the last front and its sorted copy; ekeys: the weights alpha_c
+        o_d64 = take(n2 * 8);
+        o_rhat = take(nr * m * 4);
+        o_rho = take(nr * 4);
+        o_llist = take(2 * n2 * 4);
+        o_ekeys = take((n2 + 1) * 8);
     }
     int64_t o_colpre = take(ncb * (m - 1) * colprep_obj_bytes((int)(m - 1)));
     int64_t o_D = take(ntiles * 4096);
@@ -267,15 +277,15 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         d->hist = (int32_t*)(base + o_hist);
         d->flag = (int32_t*)(base + o_flag);
         d->pi = in.mode == MODE_SELECT ? (int32_t*)(base + o_pi) : nullptr;
-        d->d64 = in.mode == MODE_SELECT ? (double*)(base + o_d64) : nullptr;
-        d->rhat = in.mode == MODE_SELECT ? (float*)(base + o_rhat) : nullptr;
+        d->d64 = (in.mode == MODE_SELECT || in.mode == MODE_HYPE) ? (double*)(base + o_d64) : nullptr;
+        d->rhat = (in.mode == MODE_SELECT || in.mode == MODE_HYPE) ? (float*)(base + o_rhat) : nullptr;
         d->flagged = in.mode == MODE_SELECT ? (int32_t*)(base + o_flagged) : nullptr;
-        d->rho = in.mode == MODE_SELECT ? (int32_t*)(base + o_rho) : nullptr;
+        d->rho = (in.mode == MODE_SELECT || in.mode == MODE_HYPE) ? (int32_t*)(base + o_rho) : nullptr;
         d->lcnt = in.mode == MODE_SELECT ? (int32_t*)(base + o_lcnt) : nullptr;
         d->loff = in.mode == MODE_SELECT ? (int32_t*)(base + o_loff) : nullptr;
-        d->llist = in.mode == MODE_SELECT ? (int32_t*)(base + o_llist) : nullptr;
+        d->llist = (in.mode == MODE_SELECT || in.mode == MODE_HYPE) ? (int32_t*)(base + o_llist) : nullptr;
         d->fen = in.mode == MODE_SELECT ? (int32_t*)(base + o_fen) : nullptr;
-        d->ekeys = in.mode == MODE_SELECT ? (unsigned long long*)(base + o_ekeys) : nullptr;
+        d->ekeys = (in.mode == MODE_SELECT || in.mode == MODE_HYPE) ? (unsigned long long*)(base + o_ekeys) : nullptr;
         d->elist = in.mode == MODE_SELECT ? (int32_t*)(base + o_elist) : nullptr;
         d->nhist = in.mode == MODE_SELECT ? (int32_t*)(base + o_nhist) : nullptr;
         d->rord = in.mode == MODE_SELECT ? (int32_t*)(base + o_rord) : nullptr;

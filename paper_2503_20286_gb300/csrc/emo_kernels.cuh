@@ -196,6 +196,7 @@ __global__ void k_rescan(Plan* plan);
 __global__ void k_csr(Plan* plan);
 __global__ void k_niche(Plan* plan);
 __global__ void k_niche_oneshot(Plan* plan);
+__global__ void k_hype(Plan* plan);
 __global__ void k_finish(Plan* plan);
 
 // Dominance kernels, one instantiation per objective count (k_dominance.cu).

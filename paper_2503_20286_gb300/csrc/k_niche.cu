@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_finish(Plan* plan)
     const int64_t stride = (int64_t)g.size * blockDim.x;
     bool ok = ld_volatile(&sc->status) == 0;
     int ns = 0;
-    if (ok && in.mode == MODE_SELECT) {
+    if (ok && (in.mode == MODE_SELECT || in.mode == MODE_HYPE)) {
         const int l = sc->l;
         ns = group_compact(
             d, g, budget, n2, [&](int64_t i) { return __ldcg(&d.rank_o[i]) < l || __ldcg(&d.flag[i]) != 0; },

@@ -65,6 +65,8 @@ def test_host_argument_checks_reject_before_launch(lib):
     assert L.emo_nd_rank(p, 10, 3, 11, p, None, p, 1 << 20, None) == 1                    # n_keep > n2
     assert L.emo_nsga3_select_batch(None, 1, p, 1 << 20, None) == 1
     assert L.emo_nsga3_select_ex(p, 10, 3, p, 5, 5, 0, 0, 2, p, None, None, p, 1 << 20, None) == 1  # niche mode
+    assert L.emo_hype_select(p, 10, 3, p, None, 100, 5, p, None, None, p, 1 << 20, None) == 1        # no samples
+    assert L.emo_hype_select(p, 10, 3, p, p, 0, 5, p, None, None, p, 1 << 20, None) == 1           # s = 0
     assert L.emo_workspace_size(2, 0, 3, 5) == 0
     assert L.emo_workspace_size(2, 10, 1, 5) == 0
     assert L.emo_workspace_size(7, 10, 3, 5) == 0
