@@ -10,8 +10,9 @@
 //       one sample per thread; the weights alpha_c for c <= k (one thread, in
 //       order: lambda_1 = 1, lambda_c = (k - c + 1) / (n2 - c + 1), alpha_c =
 //       (lambda_1 ... lambda_c) / c; alpha_c = 0 beyond k);
-//   (D) each point of L: its contribution, vol / s times the sum of
-//       alpha_{c_i} over the samples it dominates in sample order (double);
+//   (D) each point of L (one warp, samples staged in shared memory): its
+//       contribution, vol / s times the sum of alpha_{c_i} over the samples
+//       it dominates in sample order (double);
 //   (E) L sorted stably by (contribution descending) with 64-bit radix passes;
 //       its first n_keep - |P| points are flagged as survivors.
 #include <cfloat>
@@ -22,6 +23,34 @@
 namespace emo {
 
 constexpr int kHypeTile = 6144;  // floats of the point tile in shared memory
+
+// Points of a shared-memory tile that weakly dominate sample smp (compile-time m).
+template <int M>
+__device__ __forceinline__ int count_dominators(const float* __restrict__ pts, int np, const float* smp)
+{
+    float sv[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) sv[k] = smp[k];
+    int cnt = 0;
+#pragma unroll 4
+    for (int q = 0; q < np; ++q) {
+        bool dom = true;
+#pragma unroll
+        for (int k = 0; k < M; ++k) dom &= pts[q * M + k] <= sv[k];
+        cnt += dom ? 1 : 0;
+    }
+    return cnt;
+}
+__device__ __forceinline__ int count_dominators_rt(const float* __restrict__ pts, int np, const float* smp, int m)
+{
+    int cnt = 0;
+    for (int q = 0; q < np; ++q) {
+        bool dom = true;
+        for (int k = 0; k < m; ++k) dom &= pts[q * m + k] <= smp[k];
+        cnt += dom ? 1 : 0;
+    }
+    return cnt;
+}
 
 // Order-preserving 64-bit key of a double, largest first (0 and -0 equal).
 __device__ __forceinline__ unsigned long long hype_desc_key(double v)
@@ -100,11 +129,14 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_hype(Plan* plan)
         if (si < ns) {
             float smp[kMaxM];
             for (int k = 0; k < m; ++k) smp[k] = __ldcg(&d.rhat[si * m + k]);
-            int cnt = 0;
-            for (int q = 0; q < np; ++q) {
-                bool dom = true;
-                for (int k = 0; k < m && dom; ++k) dom = s_pts[q * m + k] <= smp[k];
-                cnt += dom ? 1 : 0;
+            int cnt;
+            switch (m) {
+            case 2: cnt = count_dominators<2>(s_pts, (int)np, smp); break;
+            case 3: cnt = count_dominators<3>(s_pts, (int)np, smp); break;
+            case 4: cnt = count_dominators<4>(s_pts, (int)np, smp); break;
+            case 5: cnt = count_dominators<5>(s_pts, (int)np, smp); break;
+            case 6: cnt = count_dominators<6>(s_pts, (int)np, smp); break;
+            default: cnt = count_dominators_rt(s_pts, (int)np, smp, m);
             }
             if (cnt) atomicAdd(&d.rho[si], cnt);
         }
@@ -122,25 +154,51 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_hype(Plan* plan)
     }
     if (!group_sync(sc, g.size, budget)) return;
 
-    // (D) contributions of the points of front l
+    // (D) contributions of the points of front l: one warp per point; the
+    // samples and their counts pass through shared memory in tiles, each lane
+    // tests one sample, and the weights of the dominated ones are added in
+    // sample order (ballot bits ascending)
     double vol = 1.0;
     for (int k = 0; k < m; ++k) vol = __dmul_rn(vol, __dsub_rn((double)vref[k], (double)fl[k]));
-    for (int64_t t = t0; t < nL; t += stride) {
-        const int64_t p = __ldcg(&L[t]);
-        float f[kMaxM];
-        for (int k = 0; k < m; ++k) f[k] = F[p * m + k];
-        double v = 0.0;
-        for (int i = 0; i < ns; ++i) {
-            bool dom = true;
-            for (int k = 0; k < m && dom; ++k) dom = f[k] <= __ldcg(&d.rhat[(int64_t)i * m + k]);
-            if (dom) {
-                const int c = __ldcg(&d.rho[i]);  // >= 1: p itself
-                if (c <= kdrop) v = __dadd_rn(v, __ldcg(&alpha[c]));
+    {
+        const int lane = tid & 31, nwb = blockDim.x >> 5;
+        const int ts = kHypeTile / (m + 1);  // samples per tile (m floats and a count each)
+        float* s_smp = s_pts;
+        int* s_cnt = reinterpret_cast<int*>(s_pts + ts * m);
+        const int64_t nw_all = (int64_t)g.size * nwb, gw = (int64_t)g.rank * nwb + (tid >> 5);
+        for (int64_t b0 = 0; b0 < nL; b0 += nw_all) {  // the same trip count in every CTA
+            const int64_t t = b0 + gw;
+            const bool has = t < nL;
+            const int64_t p = has ? __ldcg(&L[t]) : 0;
+            float f[kMaxM];
+            for (int k = 0; k < m; ++k) f[k] = has ? F[p * m + k] : 0.0f;
+            double v = 0.0;
+            for (int i0 = 0; i0 < ns; i0 += ts) {
+                const int nt = min(ts, ns - i0);
+                __syncthreads();
+                for (int e = tid; e < nt * m; e += blockDim.x) s_smp[e] = __ldcg(&d.rhat[(int64_t)i0 * m + e]);
+                for (int e = tid; e < nt; e += blockDim.x) s_cnt[e] = __ldcg(&d.rho[i0 + e]);
+                __syncthreads();
+                if (!has) continue;
+                for (int j0 = 0; j0 < nt; j0 += 32) {
+                    const int j = j0 + lane;
+                    bool dom = j < nt;
+                    for (int k = 0; k < m; ++k) dom &= f[k] <= s_smp[(j < nt ? j : 0) * m + k];
+                    unsigned mask = __ballot_sync(0xffffffffu, dom);
+                    while (mask) {
+                        const int b = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const int c = s_cnt[j0 + b];  // >= 1: p itself
+                        if (c <= kdrop) v = __dadd_rn(v, __ldcg(&alpha[c]));
+                    }
+                }
+            }
+            if (has && lane == 0) {
+                const double hv = __ddiv_rn(__dmul_rn(v, vol), (double)ns);
+                d.d64[p] = hv;
+                if (in.hv_out) in.hv_out[p] = hv;
             }
         }
-        const double hv = __ddiv_rn(__dmul_rn(v, vol), (double)ns);
-        d.d64[p] = hv;
-        if (in.hv_out) in.hv_out[p] = hv;
     }
     if (in.hv_out)
         for (int64_t i = t0; i < n2; i += stride)
