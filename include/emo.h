@@ -239,6 +239,24 @@ emo_status emo_nsga3_select_noalloc(const float* F, int64_t n2, int32_t m, const
  * last used on it (EMO_OK when every problem finished cleanly). */
 emo_status emo_workspace_status(const void* ws, emo_stream_t stream, int32_t* status_out);
 
+/* The first status a device-side check reported on the current device
+ * (EMO_ERR_NONFINITE, EMO_ERR_INVALID_ARG, EMO_ERR_TIMEOUT from any call,
+ * 0 when none) since the last read; waits for `stream`'s prior work and
+ * clears the word, like cudaGetLastError. */
+emo_status emo_get_last_device_status(emo_stream_t stream, int32_t* status_out);
+
+/* Offline tuning of the launch shapes for populations of m objectives and
+ * about n2 points (same floor(log2 n2)) on the current device: the
+ * association kernel's blocks per SM, timed on a synthetic population (a
+ * sphere-shaped front and n2/2 directions on the simplex) over the
+ * candidates 2, 4, 8, 16, 32. It allocates device memory and synchronises,
+ * so it belongs outside timed regions and graph captures. With a non-null
+ * `cache_path`, results found in that text file ("m bucket blocks" lines)
+ * are loaded and reused, and a new result is appended. Later calls of the
+ * same process use the tuned shape; results do not depend on it.
+ * EMO_ERR_INVALID_ARG for n2 < 64 or sizes out of range. */
+emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path);
+
 /* Bounded-wait budget (in SM clock cycles) for the device-side barriers of
  * later calls in this process; 0 restores the default (about 2 s). */
 void emo_set_spin_budget(int64_t cycles);

@@ -82,6 +82,10 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             L.emo_nd_rank.argtypes = [vp, i64, i32, i64, vp, vp, vp, sz, vp]
             L.emo_nsga3_select.restype = ctypes.c_int
             L.emo_nsga3_select.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp, vp, sz, vp]
+            L.emo_autotune.restype = ctypes.c_int
+            L.emo_autotune.argtypes = [i32, i64, ctypes.c_char_p]
+            L.emo_get_last_device_status.restype = ctypes.c_int
+            L.emo_get_last_device_status.argtypes = [vp, vp]
             L.emo_hype_select.restype = ctypes.c_int
             L.emo_hype_select.argtypes = [vp, i64, i32, vp, vp, i32, i64, vp, vp, vp, vp, sz, vp]
             L.emo_nsga3_select_ex.restype = ctypes.c_int
@@ -274,6 +278,18 @@ def emo_nsga3_select_batch(problems, ws: torch.Tensor | None = None, stream=None
 def emo_workspace_status(ws: torch.Tensor, stream=None) -> int:
     out = ctypes.c_int32(0)
     _check(lib().emo_workspace_status(_ptr(ws), _stream(stream), ctypes.byref(out)), "emo_workspace_status")
+    return int(out.value)
+
+
+def emo_autotune(m: int, n2: int, cache_path: str | None = None) -> None:
+    """Offline tuning of the launch shapes for (m, about n2) on the current device."""
+    _check(lib().emo_autotune(int(m), int(n2), cache_path.encode() if cache_path else None), "emo_autotune")
+
+
+def emo_get_last_device_status(stream=None) -> int:
+    """The first device-detected status since the last read (cleared by the read)."""
+    out = ctypes.c_int32(0)
+    _check(lib().emo_get_last_device_status(_stream(stream), ctypes.byref(out)), "emo_get_last_device_status")
     return int(out.value)
 
 

@@ -2,15 +2,19 @@
 // the launch sequence of each call. All device work is stream ordered; no
 // call synchronises except emo_workspace_status.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <string>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "emo_kernels.cuh"
+#include "emo_launch.cuh"
 
 using namespace emo;
 
@@ -147,6 +151,27 @@ cudaError_t coop(const void* fn, int G, size_t smem, cudaStream_t s, Plan* plan)
 
 // Launch the whole pipeline for problems already laid out in `ins` (ordered
 // by objective count).
+// Launch shapes chosen by emo_autotune, per (device, m, floor(log2 n2)):
+// the association kernel's blocks per SM. 0 = the default (8).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+std::atomic<int> g_force_assoc_bps{0};  // set only while emo_autotune times a candidate
+
+int size_bucket(int64_t n2)
+{
+    int b = 0;
+    while ((int64_t(1) << (b + 1)) <= n2) ++b;
+    return b;
+}
+
+int assoc_blocks_per_sm(int dev, int m, int64_t n2)
+{
+    if (int f = g_force_assoc_bps.load()) return f;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(dev, m, size_bucket(n2)));
+    return it == g_tune.end() ? 8 : it->second;
+}
+
 emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t s)
 {
     DevInfo di = dev_info();
@@ -206,7 +231,12 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
         sm.mark("stats");
         std::vector<int> m_of(nprob);
         for (int p = 0; p < nprob; ++p) m_of[p] = ins[p].m;
-        if (launch_assoc(plan, nprob, m_of.data(), di.sms, s) != cudaSuccess) return EMO_ERR_CUDA;
+        int dev = 0, big = 0;
+        cudaGetDevice(&dev);
+        for (int p = 1; p < nprob; ++p)
+            if (ins[p].n2 > ins[big].n2) big = p;
+        const int bps = assoc_blocks_per_sm(dev, ins[big].m, ins[big].n2);
+        if (launch_assoc(plan, nprob, m_of.data(), di.sms, bps, s) != cudaSuccess) return EMO_ERR_CUDA;
         sm.mark("assoc");
         k_rescan<<<di.sms * 2, 256, 0, s>>>(plan);
         if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
@@ -390,6 +420,99 @@ emo_status emo_workspace_status(const void* ws, emo_stream_t stream, int32_t* st
 }
 
 void emo_set_spin_budget(int64_t cycles) { g_spin_budget.store(cycles > 0 ? cycles : 0); }
+
+emo_status emo_get_last_device_status(emo_stream_t stream, int32_t* status_out)
+{
+    if (!status_out) return EMO_ERR_INVALID_ARG;
+    return sticky_status((cudaStream_t)stream, status_out, true) == cudaSuccess ? EMO_OK : EMO_ERR_CUDA;
+}
+
+emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path)
+{
+    if (!sizes_ok(n2, m) || n2 < 64) return EMO_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EMO_ERR_CUDA;
+    const auto key = std::make_tuple(dev, (int)m, size_bucket(n2));
+    if (cache_path) {  // earlier results: lines "m bucket blocks_per_sm"
+        if (FILE* fh = std::fopen(cache_path, "r")) {
+            int cm = 0, cb = 0, cv = 0;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            while (std::fscanf(fh, "%d %d %d", &cm, &cb, &cv) == 3)
+                if (cv >= 1 && cv <= 64) g_tune[std::make_tuple(dev, cm, cb)] = cv;
+            std::fclose(fh);
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (g_tune.count(key)) return EMO_OK;
+    }
+    // a synthetic population: a sphere-shaped front with a spread of
+    // distances, and n2 / 2 directions drawn on the simplex (fixed seed)
+    const int64_t n_r = std::max<int64_t>(1, std::min<int64_t>(n2 / 2, 1 << 20));
+    std::vector<float> F((size_t)(n2 * m)), R((size_t)(n_r * m));
+    uint64_t x = 0x9E3779B97F4A7C15ull;
+    auto uni = [&]() {  // splitmix64 -> (0, 1)
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    for (int64_t i = 0; i < n2; ++i) {
+        double nrm = 0.0, v[kMaxM];
+        for (int k = 0; k < m; ++k) { v[k] = -std::log(uni()); nrm += v[k] * v[k]; }
+        const double scale = (1.0 + 0.5 * uni()) / std::sqrt(nrm);
+        for (int k = 0; k < m; ++k) F[(size_t)(i * m + k)] = (float)(v[k] * scale);
+    }
+    for (int64_t j = 0; j < n_r; ++j) {
+        double sum = 0.0, v[kMaxM];
+        for (int k = 0; k < m; ++k) { v[k] = -std::log(uni()); sum += v[k]; }
+        for (int k = 0; k < m; ++k) R[(size_t)(j * m + k)] = (float)(v[k] / sum);
+    }
+    const size_t wsb = emo_workspace_size(EMO_OP_NSGA3_SELECT, n2, m, (int32_t)n_r);
+    if (wsb == 0) return EMO_ERR_INVALID_ARG;
+    void *dF = nullptr, *dR = nullptr, *dS = nullptr, *dW = nullptr;
+    emo_status st = EMO_OK;
+    int best = 8;
+    float best_ms = INFINITY;
+    if (cudaMalloc(&dF, F.size() * 4) != cudaSuccess || cudaMalloc(&dR, R.size() * 4) != cudaSuccess ||
+        cudaMalloc(&dS, (size_t)(n2 / 2 + 1) * 4) != cudaSuccess || cudaMalloc(&dW, wsb) != cudaSuccess ||
+        cudaMemcpy(dF, F.data(), F.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dR, R.data(), R.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        st = EMO_ERR_CUDA;
+    } else {
+        const int prev_timing = g_timing.exchange(1);
+        for (int cand : {2, 4, 8, 16, 32}) {  // the association stage, best of three calls
+            g_force_assoc_bps.store(cand);
+            float ms_best = INFINITY;
+            for (int rep = 0; rep < 3 && st == EMO_OK; ++rep) {
+                st = emo_nsga3_select((const float*)dF, n2, m, (const float*)dR, (int32_t)n_r, n2 / 2, 1, rep,
+                                      (int32_t*)dS, nullptr, dW, wsb, nullptr);
+                float ms[32];
+                const char* names[32];
+                const int ns = st == EMO_OK ? emo_stage_times(ms, names, 32) : -1;
+                if (ns < 0) st = st == EMO_OK ? EMO_ERR_CUDA : st;
+                for (int i = 0; i < ns; ++i)
+                    if (std::strcmp(names[i], "assoc") == 0) ms_best = std::min(ms_best, ms[i]);
+            }
+            if (st != EMO_OK) break;
+            if (ms_best < best_ms) { best_ms = ms_best; best = cand; }
+        }
+        g_force_assoc_bps.store(0);
+        g_timing.store(prev_timing);
+    }
+    cudaFree(dF); cudaFree(dR); cudaFree(dS); cudaFree(dW);
+    if (st != EMO_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = best;
+    }
+    if (cache_path)
+        if (FILE* fh = std::fopen(cache_path, "a")) {
+            std::fprintf(fh, "%d %d %d\n", (int)m, size_bucket(n2), best);
+            std::fclose(fh);
+        }
+    return EMO_OK;
+}
 
 const char* emo_status_string(int status)
 {

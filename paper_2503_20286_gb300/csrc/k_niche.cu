@@ -11,6 +11,7 @@
 // from the ascending candidate list with a Fenwick tree per list, so a draw
 // costs O(log |C_j|).
 #include "emo_kernels.cuh"
+#include "emo_launch.cuh"
 #include "group_radix.cuh"
 
 namespace emo {
@@ -411,6 +412,19 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_niche_oneshot(Plan* plan)
 }
 
 // ------------------------------------------------------------ k_finish
+__device__ int32_t g_sticky_status;  // first failure since the last read (per device)
+
+cudaError_t sticky_status(cudaStream_t s, int32_t* out, bool clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_sticky_status, sizeof(int32_t), 0, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && clear) {
+        static const int32_t zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_sticky_status, &zero, sizeof(int32_t), 0, cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
 // Survivors (ascending indices of P and the picked members), the info block
 // and the optional intermediates.
 __global__ void __launch_bounds__(kCoopThreads, 1) k_finish(Plan* plan)
@@ -457,7 +471,10 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_finish(Plan* plan)
     }
     if (g.rank == 0 && tid == 0) {
         const int st = ld_volatile(&sc->status);
-        if (st) atomicCAS(&plan->status, 0, st);
+        if (st) {
+            atomicCAS(&plan->status, 0, st);
+            atomicCAS(&g_sticky_status, 0, st);
+        }
         if (in.info) {
             emo_select_info info;
             info.status = st;

@@ -15,6 +15,7 @@
 //     rigorous error band of the best are re-evaluated with the FP64
 //     perpendicular distance d^2 = sum (f_k - t r_k)^2, t = f.r / r.r.
 #include "emo_kernels.cuh"
+#include "emo_launch.cuh"
 #include "group_radix.cuh"
 
 namespace emo {
@@ -495,12 +496,12 @@ __global__ void __launch_bounds__(256) k_rescan(Plan* plan)
 }
 
 // Host launcher: one instantiation per objective count.
-cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, cudaStream_t s)
+cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, int blocks_per_sm, cudaStream_t s)
 {
     for (int p = 0; p < nprob;) {
         int q = p;
         while (q < nprob && m_of[q] == m_of[p]) ++q;
-        const unsigned grid = (unsigned)sms * 8;
+        const unsigned grid = (unsigned)sms * (unsigned)(blocks_per_sm > 0 ? blocks_per_sm : 8);
         switch (m_of[p]) {
 #define X(MM) \
     case MM: k_assoc_m<MM><<<grid, 256, 0, s>>>(plan, p, q); break;
@@ -513,6 +514,11 @@ cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, cudaSt
         p = q;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, cudaStream_t s)
+{
+    return launch_assoc(plan, nprob, m_of, sms, 8, s);  // the default shape: 8 blocks per SM
 }
 
 }  // namespace emo

@@ -66,6 +66,9 @@ def test_host_argument_checks_reject_before_launch(lib):
     assert L.emo_nsga3_select_batch(None, 1, p, 1 << 20, None) == 1
     assert L.emo_nsga3_select_ex(p, 10, 3, p, 5, 5, 0, 0, 2, p, None, None, p, 1 << 20, None) == 1  # niche mode
     assert L.emo_hype_select(p, 10, 3, p, None, 100, 5, p, None, None, p, 1 << 20, None) == 1        # no samples
+    assert L.emo_autotune(3, 10, None) == 1                                                          # n2 < 64
+    assert L.emo_autotune(1, 1000, None) == 1                                                        # m < 2
+    assert L.emo_get_last_device_status(None, None) == 1
     assert L.emo_hype_select(p, 10, 3, p, p, 0, 5, p, None, None, p, 1 << 20, None) == 1           # s = 0
     assert L.emo_workspace_size(2, 0, 3, 5) == 0
     assert L.emo_workspace_size(2, 10, 1, 5) == 0
