@@ -246,14 +246,18 @@ emo_status emo_workspace_status(const void* ws, emo_stream_t stream, int32_t* st
 emo_status emo_get_last_device_status(emo_stream_t stream, int32_t* status_out);
 
 /* Offline tuning of the launch shapes for populations of m objectives and
- * about n2 points (same floor(log2 n2)) on the current device: the
+ * about n2 points (same floor(log2 n2)) on the current device's
+ * architecture: the
  * association kernel's blocks per SM, timed on a synthetic population (a
  * sphere-shaped front and n2/2 directions on the simplex) over the
  * candidates 2, 4, 8, 16, 32. It allocates device memory and synchronises,
  * so it belongs outside timed regions and graph captures. With a non-null
- * `cache_path`, results found in that text file ("m bucket blocks" lines)
- * are loaded and reused, and a new result is appended. Later calls of the
- * same process use the tuned shape; results do not depend on it.
+ * `cache_path`, results found in that text file (lines "arch m bucket
+ * blocks", arch = 10 * major + minor compute capability, bucket =
+ * floor(log2 n2)) are loaded and reused, and a new result is appended. Later
+ * calls of the same process use the tuned shape, and the first selection of
+ * a process loads the file named by the environment variable
+ * EMO_AUTOTUNE_CACHE, if set; survivors do not depend on the shape.
  * EMO_ERR_INVALID_ARG for n2 < 64 or sizes out of range. */
 emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path);
 

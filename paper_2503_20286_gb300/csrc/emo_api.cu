@@ -151,8 +151,9 @@ cudaError_t coop(const void* fn, int G, size_t smem, cudaStream_t s, Plan* plan)
 
 // Launch the whole pipeline for problems already laid out in `ins` (ordered
 // by objective count).
-// Launch shapes chosen by emo_autotune, per (device, m, floor(log2 n2)):
-// the association kernel's blocks per SM. 0 = the default (8).
+// Launch shapes chosen by emo_autotune, per (compute capability as
+// 10 * major + minor, m, floor(log2 n2)): the association kernel's blocks
+// per SM. Absent = the default (8).
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, int> g_tune;
 std::atomic<int> g_force_assoc_bps{0};  // set only while emo_autotune times a candidate
@@ -164,11 +165,34 @@ int size_bucket(int64_t n2)
     return b;
 }
 
+int device_arch(int dev)
+{
+    int ma = 0, mi = 0;
+    cudaDeviceGetAttribute(&ma, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&mi, cudaDevAttrComputeCapabilityMinor, dev);
+    return ma * 10 + mi;
+}
+
+// Cache file: one "arch m bucket blocks_per_sm" line per tuned shape.
+void load_tune_cache(const char* path)
+{
+    FILE* fh = path ? std::fopen(path, "r") : nullptr;
+    if (!fh) return;
+    int ca = 0, cm = 0, cb = 0, cv = 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    while (std::fscanf(fh, "%d %d %d %d", &ca, &cm, &cb, &cv) == 4)
+        if (cv >= 1 && cv <= 64) g_tune[std::make_tuple(ca, cm, cb)] = cv;
+    std::fclose(fh);
+}
+
 int assoc_blocks_per_sm(int dev, int m, int64_t n2)
 {
     if (int f = g_force_assoc_bps.load()) return f;
+    static std::once_flag env_once;  // shapes tuned by earlier processes
+    std::call_once(env_once, [] { load_tune_cache(std::getenv("EMO_AUTOTUNE_CACHE")); });
+    const int arch = device_arch(dev);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune.find(std::make_tuple(dev, m, size_bucket(n2)));
+    auto it = g_tune.find(std::make_tuple(arch, m, size_bucket(n2)));
     return it == g_tune.end() ? 8 : it->second;
 }
 
@@ -432,15 +456,10 @@ emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path)
     if (!sizes_ok(n2, m) || n2 < 64) return EMO_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return EMO_ERR_CUDA;
-    const auto key = std::make_tuple(dev, (int)m, size_bucket(n2));
-    if (cache_path) {  // earlier results: lines "m bucket blocks_per_sm"
-        if (FILE* fh = std::fopen(cache_path, "r")) {
-            int cm = 0, cb = 0, cv = 0;
-            std::lock_guard<std::mutex> lk(g_tune_mu);
-            while (std::fscanf(fh, "%d %d %d", &cm, &cb, &cv) == 3)
-                if (cv >= 1 && cv <= 64) g_tune[std::make_tuple(dev, cm, cb)] = cv;
-            std::fclose(fh);
-        }
+    const int arch = device_arch(dev);
+    const auto key = std::make_tuple(arch, (int)m, size_bucket(n2));
+    if (cache_path) {
+        load_tune_cache(cache_path);
         std::lock_guard<std::mutex> lk(g_tune_mu);
         if (g_tune.count(key)) return EMO_OK;
     }
@@ -508,7 +527,7 @@ emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path)
     }
     if (cache_path)
         if (FILE* fh = std::fopen(cache_path, "a")) {
-            std::fprintf(fh, "%d %d %d\n", (int)m, size_bucket(n2), best);
+            std::fprintf(fh, "%d %d %d %d\n", arch, (int)m, size_bucket(n2), best);
             std::fclose(fh);
         }
     return EMO_OK;

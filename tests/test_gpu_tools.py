@@ -22,7 +22,9 @@ def test_autotune_writes_and_reuses_the_cache_and_keeps_results(tmp_path):
     path = str(tmp_path / "tune.txt")
     emo.emo_autotune(3, 20000, path)
     lines = open(path).read().split()
-    assert len(lines) == 3 and lines[0] == "3" and lines[1] == "14" and int(lines[2]) in (2, 4, 8, 16, 32)
+    major, minor = torch.cuda.get_device_capability()
+    assert len(lines) == 4 and lines[0] == str(10 * major + minor) and lines[1:3] == ["3", "14"]
+    assert int(lines[3]) in (2, 4, 8, 16, 32)
     emo.emo_autotune(3, 20000, path)               # found in the cache: nothing appended
     assert open(path).read().split() == lines
     p = wl.config(1)                                # 2N = 20,000, M = 3: runs with the tuned shape
