@@ -11,6 +11,14 @@ Functions follow the paper (arXiv 2503.20286):
     perpendicular-distance association of Section IV-A.
   * ``philox4x32_10`` -- the counter-based generator whose stream breaks the
     ties of the niching step (Salmon et al., SC'11).
+
+``emo_oracle_ops.c`` holds the generation around the selection and the
+second algorithm family:
+  * ``sbx_pair`` / ``pm_value`` / ``variation`` -- random mating, simulated
+    binary crossover and polynomial mutation (Appendix S.I).
+  * ``pbi`` / ``moead_select`` / ``moead_offspring`` -- the TensorMOEA/D
+    environmental selection of Algorithm S.8 and its reproduction.
+  * ``igd`` -- inverted generational distance to a reference front.
 """
 from __future__ import annotations
 
@@ -23,6 +31,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "emo_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "emo_oracle_ops.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -32,11 +41,12 @@ NOT_RANKED = np.iinfo(np.int32).max
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction). Returns the .so path."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+    if (not force and os.path.exists(_LIB_PATH)
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src) for src in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-                           _SRC, "-o", tmp, "-lm"])
+                           *_SRCS, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -81,6 +91,23 @@ def lib():
                                                  ctypes.c_void_p]
             _lib.oracle_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             _lib.oracle_dominates.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            vp, i64, dbl, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+            _lib.oracle_sbx_pair.restype = None
+            _lib.oracle_sbx_pair.argtypes = [dbl, dbl, dbl, dbl, vp, vp]
+            _lib.oracle_pm_value.restype = dbl
+            _lib.oracle_pm_value.argtypes = [dbl, dbl, dbl, dbl, dbl]
+            _lib.oracle_variation.restype = ctypes.c_int
+            _lib.oracle_variation.argtypes = [vp, i64, i64, vp, vp, i64, u64, u64, dbl, dbl, dbl, dbl, vp, vp]
+            _lib.oracle_pbi.restype = dbl
+            _lib.oracle_pbi.argtypes = [vp, vp, vp, ctypes.c_int, dbl]
+            _lib.oracle_moead_select.restype = ctypes.c_int
+            _lib.oracle_moead_select.argtypes = [vp, vp, vp, vp, i64, i64, ctypes.c_int, vp, vp, vp,
+                                                 ctypes.c_int32, dbl, vp, vp, vp]
+            _lib.oracle_moead_offspring.restype = ctypes.c_int
+            _lib.oracle_moead_offspring.argtypes = [vp, i64, i64, vp, vp, vp, ctypes.c_int32, u64, u64,
+                                                    dbl, dbl, dbl, vp, vp]
+            _lib.oracle_igd.restype = dbl
+            _lib.oracle_igd.argtypes = [vp, i64, ctypes.c_int, vp, i64]
         return _lib
 
 
@@ -191,3 +218,84 @@ def hype_select(F, v_ref, U, n_keep: int):
     if rc != 0:
         raise OracleError(f"oracle_hype_select status {rc}")
     return surv, vhv, int(last[0])
+
+
+def sbx_pair(x1: float, x2: float, mu: float, eta_c: float) -> tuple[float, float]:
+    """The two SBX children of one variable (Appendix S.I), FP64."""
+    c1, c2 = ctypes.c_double(), ctypes.c_double()
+    lib().oracle_sbx_pair(float(x1), float(x2), float(mu), float(eta_c), ctypes.byref(c1), ctypes.byref(c2))
+    return c1.value, c2.value
+
+
+def pm_value(x: float, lo: float, hi: float, mu: float, eta_m: float) -> float:
+    """Polynomial mutation of one variable (Appendix S.I, original form), FP64."""
+    return lib().oracle_pm_value(float(x), float(lo), float(hi), float(mu), float(eta_m))
+
+
+def variation(X, lo, hi, n_off: int, seed: int, generation: int, eta_c: float = 20.0, eta_m: float = 20.0,
+              p_c: float = 1.0, p_m: float | None = None):
+    """Offspring of one generation (random mating, SBX, PM) and the parent
+    index pairs. ``p_m`` defaults to 1/D."""
+    X = _f32(X)
+    n, d = X.shape
+    lo = _f32(np.broadcast_to(np.asarray(lo, np.float32), (d,)))
+    hi = _f32(np.broadcast_to(np.asarray(hi, np.float32), (d,)))
+    p_m = 1.0 / d if p_m is None else p_m
+    out = np.zeros((n_off, d), np.float32)
+    parents = np.zeros(((n_off + 1) // 2, 2), np.int32)
+    rc = lib().oracle_variation(_p(X), n, d, _p(lo), _p(hi), n_off, seed & 0xFFFFFFFFFFFFFFFF,
+                                generation & 0xFFFFFFFFFFFFFFFF, eta_c, eta_m, p_c, p_m, _p(out), _p(parents))
+    if rc != 0:
+        raise OracleError(f"oracle_variation status {rc}")
+    return out, parents
+
+
+def pbi(f, w, z, theta: float) -> float:
+    """PBI aggregation d1 + theta d2 of one objective vector (Section IV-B)."""
+    f, w, z = _f32(f).reshape(-1), _f32(w).reshape(-1), _f32(z).reshape(-1)
+    return lib().oracle_pbi(_p(f), _p(w), _p(z), f.shape[0], float(theta))
+
+
+def moead_select(X, F1, O, F2, z, W, I_nb, theta: float = 5.0):
+    """TensorMOEA/D environmental selection (Algorithm S.8): X_next, F_next,
+    the updated ideal point and, per subproblem, the offspring taken (-1 when
+    the current solution stays)."""
+    X, F1, O, F2, W = _f32(X), _f32(F1), _f32(O), _f32(F2), _f32(W)
+    z = _f32(z).reshape(-1).copy()
+    I_nb = np.ascontiguousarray(I_nb, dtype=np.int32)
+    n, d = X.shape
+    m = F1.shape[1]
+    Xn = np.zeros_like(X)
+    Fn = np.zeros_like(F1)
+    win = np.zeros(n, np.int32)
+    rc = lib().oracle_moead_select(_p(X), _p(F1), _p(O), _p(F2), n, d, m, _p(z), _p(W), _p(I_nb),
+                                   I_nb.shape[1], float(theta), _p(Xn), _p(Fn), _p(win))
+    if rc != 0:
+        raise OracleError(f"oracle_moead_select status {rc}")
+    return Xn, Fn, z, win
+
+
+def moead_offspring(X, lo, hi, I_nb, seed: int, generation: int, eta_c: float = 20.0, eta_m: float = 20.0,
+                    p_m: float | None = None):
+    """One offspring per subproblem from two random neighbours (Algorithm S.7
+    reproduction, all subproblems at once) and the parent pairs."""
+    X = _f32(X)
+    n, d = X.shape
+    lo = _f32(np.broadcast_to(np.asarray(lo, np.float32), (d,)))
+    hi = _f32(np.broadcast_to(np.asarray(hi, np.float32), (d,)))
+    I_nb = np.ascontiguousarray(I_nb, dtype=np.int32)
+    p_m = 1.0 / d if p_m is None else p_m
+    O = np.zeros_like(X)
+    parents = np.zeros((n, 2), np.int32)
+    rc = lib().oracle_moead_offspring(_p(X), n, d, _p(lo), _p(hi), _p(I_nb), I_nb.shape[1],
+                                      seed & 0xFFFFFFFFFFFFFFFF, generation & 0xFFFFFFFFFFFFFFFF, eta_c, eta_m, p_m,
+                                      _p(O), _p(parents))
+    if rc != 0:
+        raise OracleError(f"oracle_moead_offspring status {rc}")
+    return O, parents
+
+
+def igd(F, Ref) -> float:
+    """Inverted generational distance of population F to the front Ref."""
+    F, Ref = _f32(F), _f32(Ref)
+    return lib().oracle_igd(_p(F), F.shape[0], F.shape[1], _p(Ref), Ref.shape[0])

@@ -131,6 +131,31 @@ def das_dennis_two_layer(h1: int, h2: int, m: int) -> np.ndarray:
     return np.concatenate([outer, inner.astype(np.float32).astype(np.float64)]).astype(np.float32)
 
 
+def reference_front(h: int, m: int, shape: str) -> np.ndarray:
+    """Points of the true front for IGD: Das-Dennis directions scaled onto
+    the linear front (sum f = 0.5) or projected onto the unit sphere."""
+    w = das_dennis(h, m).astype(np.float64)
+    if shape == "linear":
+        f = 0.5 * w
+    elif shape == "sphere":
+        f = w / np.linalg.norm(w, axis=1, keepdims=True)
+    else:
+        raise ValueError(f"unknown front shape {shape!r}")
+    return f.astype(np.float32)
+
+
+def moead_neighbours(W: np.ndarray, t: int) -> np.ndarray:
+    """Indices of the ``t`` weight vectors closest to each one (Euclidean,
+    FP64, ties by index; every vector is its own first neighbour)."""
+    Wd = np.asarray(W, dtype=np.float64)
+    n = Wd.shape[0]
+    out = np.empty((n, t), dtype=np.int32)
+    for i in range(n):
+        d2 = np.sum((Wd - Wd[i]) ** 2, axis=1)
+        out[i] = np.lexsort((np.arange(n), d2))[:t]
+    return out
+
+
 def das_dennis_count(h: int, m: int) -> int:
     return math.comb(h + m - 1, m - 1)
 
