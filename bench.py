@@ -219,6 +219,63 @@ def hype_timing(emo, torch, Ft, F, n_keep, flush, stream, steps, n_samples: int 
             "ms_per_step": t, "selections_per_s": 1e3 / t, "hype_stage_ms": statistics.mean(hype)}
 
 
+def moead_inputs(h: int, m: int, d: int, t: int, seed: int):
+    """A TensorMOEA/D selection problem: Das-Dennis weights (H = h), their t
+    nearest neighbours, current and offspring populations on the sphere
+    stand-in front (uniform decision vectors), z = minimum of the current
+    objectives."""
+    from paper_2503_20286_gb300 import workloads as wl
+    W = wl.das_dennis(h, m)
+    n = W.shape[0]
+    I_nb = wl.moead_neighbours_fast(W, t)
+    X = wl.decision_vectors(n, d, seed, stream=11)
+    O = wl.decision_vectors(n, d, seed, stream=12)
+    F1 = wl.objectives_from_decisions(X, m, "sphere")
+    F2 = wl.objectives_from_decisions(O, m, "sphere")
+    z = F1.min(axis=0).astype(np.float32)
+    return X, F1, O, F2, z, W, I_nb
+
+
+def moead_timing(emo, torch, dev, flush, stream, steps, h: int = 631, m: int = 3, d: int = 12, t: int = 20):
+    """TensorMOEA/D selection (Algorithm S.8) of C(h+m-1, m-1) subproblems
+    with t neighbours: device time per call (CUDA events, L2 flushed before
+    each); the ideal point is reset before every call so each call does the
+    same work."""
+    X, F1, O, F2, z, W, I_nb = moead_inputs(h, m, d, t, seed=0x250320286)
+    n = W.shape[0]
+    T = {k: torch.from_numpy(v).to(dev) for k, v in
+         dict(X=X, F1=F1, O=O, F2=F2, z=z, W=W, I=I_nb).items()}
+    zt = T["z"].clone()
+    Xn, Fn = torch.empty_like(T["X"]), torch.empty_like(T["F1"])
+    win = torch.empty(n, dtype=torch.int32, device=dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(emo.emo_workspace_size(emo.EMO_OP_MOEAD_SELECT, n, m, t), dtype=torch.uint8, device=dev)
+
+    def call():
+        zt.copy_(T["z"])
+        emo.emo_moead_select(T["X"], T["F1"], T["O"], T["F2"], zt, T["W"], T["I"], 5.0, X_next=Xn, F_next=Fn,
+                             winner=win, status=st, ws=ws, stream=stream)
+    for _ in range(3):
+        call()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    if int(st.item()) != 0:
+        raise SystemExit("TensorMOEA/D selection failed on the device")
+    tm = statistics.mean(ms)
+    # bytes the selection must move: the taken rows of X or O and X_next, F1, F2, W, F_next, I_nb
+    nbytes = 2 * n * d * 4 + 4 * n * m * 4 + n * t * 4
+    return {"selection": "TensorMOEA/D (Algorithm S.8), PBI theta = 5", "subproblems": n, "m": m, "d": d,
+            "neighbours": t, "steps": steps, "ms_per_step": tm, "selections_per_s": 1e3 / tm,
+            "replaced": int((win >= 0).sum().item()), "algorithmic_bytes": nbytes}
+
+
 def batched_vs_plain(emo, torch, dev, rounds: int = 5):
     """64 uneven populations: one batched call replayed from a CUDA graph
     versus 64 plain calls on one stream (device time, CUDA events)."""

@@ -89,7 +89,13 @@ typedef struct {
     int32_t reserved;      /* 0 */
 } emo_problem;
 
-typedef enum { EMO_OP_DOMINANCE = 0, EMO_OP_ND_RANK = 1, EMO_OP_NSGA3_SELECT = 2, EMO_OP_HYPE_SELECT = 3 } emo_op;
+typedef enum {
+    EMO_OP_DOMINANCE = 0,
+    EMO_OP_ND_RANK = 1,
+    EMO_OP_NSGA3_SELECT = 2,
+    EMO_OP_HYPE_SELECT = 3,
+    EMO_OP_MOEAD_SELECT = 4 /* emo_workspace_size(EMO_OP_MOEAD_SELECT, n, m, T) */
+} emo_op;
 
 /* Bytes of workspace needed by `op` for a population of n2 points with m
  * objectives and n_r reference directions (n_r ignored for ranking). Returns
@@ -215,6 +221,42 @@ emo_status emo_nsga3_select_batch(const emo_problem* descs, int32_t batch, void*
 emo_status emo_hype_select(const float* F, int64_t n2, int32_t m, const float* v_ref, const float* U,
                            int32_t n_samples, int64_t n_keep, int32_t* survivors, emo_select_info* info,
                            double* hv, void* ws, size_t ws_bytes, emo_stream_t stream);
+
+/*
+ * TensorMOEA/D environmental selection (Algorithm S.8, PBI aggregation of
+ * Section IV-B): n subproblems, each with a current solution and one
+ * offspring per subproblem.
+ *   X, O       device float [n][d]: current solutions and offspring
+ *   F1, F2     device float [n][m]: their objectives (finite)
+ *   z          device float [m], in/out: the ideal point; on return
+ *              z_min = per-objective minimum of z and F2 (a zero is +0)
+ *   W          device float [n][m]: weight vectors (finite, non-zero)
+ *   I_nb       device int32 [n][T]: neighbour subproblems of each offspring
+ *              (0 <= I_nb < n; a neighbour listed twice counts once)
+ *   theta      PBI penalty (>= 0, finite; 5 is customary)
+ *   X_next, F_next  device outputs [n][d], [n][m]; X_next may be X and
+ *              F_next may be F1 (in place); neither may overlap O or F2
+ *   winner     device int32 [n] or NULL: the offspring each subproblem took,
+ *              -1 when it kept its solution
+ *   status_out device int32 or NULL: EMO_OK, EMO_ERR_INVALID_ARG (an
+ *              I_nb entry out of range) or EMO_ERR_NONFINITE (non-finite
+ *              F1, F2, W or z, or a zero weight vector); outputs are
+ *              undefined when it is not EMO_OK. Also folded into the sticky
+ *              status of emo_get_last_device_status.
+ *   ws         workspace of emo_workspace_size(EMO_OP_MOEAD_SELECT, n, m, T)
+ *              bytes, 256-byte aligned.
+ * Semantics: offspring i marks neighbour j when PBI(F2_i | W_j, z_min) <=
+ * PBI(F1_j | W_j, z_min); subproblem j then takes the first minimum, over
+ * positions i = 0 .. n-1, of PBI(f_i | W_j, z_min) where f_i = F2_i if i
+ * marked j and F1_j otherwise. PBI: d1 = |(f - z).w| / ||w||,
+ * d2 = ||(f - z) - d1 w / ||w|| ||, g = d1 + theta d2, in FP64 from the
+ * float inputs (k ascending, no contraction). Asynchronous on `stream`;
+ * argument errors are returned at once. 2 <= m <= 16, 1 <= T <= min(n, 4096).
+ */
+emo_status emo_moead_select(const float* X, const float* F1, const float* O, const float* F2, int64_t n, int64_t d,
+                            int32_t m, float* z, const float* W, const int32_t* I_nb, int32_t T, double theta,
+                            float* X_next, float* F_next, int32_t* winner, int32_t* status_out, void* ws,
+                            size_t ws_bytes, emo_stream_t stream);
 
 /*
  * emo_nsga3_select without a caller workspace, for callers that cannot

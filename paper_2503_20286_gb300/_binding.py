@@ -19,7 +19,7 @@ from . import build as _build
 EMO_OK = 0
 STATUS_NAMES = {0: "EMO_OK", 1: "EMO_ERR_INVALID_ARG", 2: "EMO_ERR_NONFINITE", 3: "EMO_ERR_WORKSPACE",
                 4: "EMO_ERR_CUDA", 5: "EMO_ERR_TIMEOUT", 6: "EMO_ERR_NOT_IMPLEMENTED"}
-EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT, EMO_OP_HYPE_SELECT = 0, 1, 2, 3
+EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT, EMO_OP_HYPE_SELECT, EMO_OP_MOEAD_SELECT = 0, 1, 2, 3, 4
 EMO_NOT_RANKED = 2147483647
 EMO_NICHE_EXACT, EMO_NICHE_ONESHOT = 0, 1
 EMO_MAX_BATCH = 128
@@ -82,6 +82,9 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             L.emo_nd_rank.argtypes = [vp, i64, i32, i64, vp, vp, vp, sz, vp]
             L.emo_nsga3_select.restype = ctypes.c_int
             L.emo_nsga3_select.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp, vp, sz, vp]
+            L.emo_moead_select.restype = ctypes.c_int
+            L.emo_moead_select.argtypes = [vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, i32, ctypes.c_double,
+                                           vp, vp, vp, vp, vp, sz, vp]
             L.emo_autotune.restype = ctypes.c_int
             L.emo_autotune.argtypes = [i32, i64, ctypes.c_char_p]
             L.emo_get_last_device_status.restype = ctypes.c_int
@@ -239,6 +242,31 @@ def emo_hype_select(F: torch.Tensor, v_ref: torch.Tensor, U: torch.Tensor, n_kee
     _check(lib().emo_hype_select(_ptr(F), n2, m, _ptr(v_ref), _ptr(U), ns, n_keep, _ptr(survivors), _ptr(info),
                                  _ptr(hv), _ptr(ws), nbytes, _stream(stream)), "emo_hype_select")
     return survivors
+
+
+def emo_moead_select(X: torch.Tensor, F1: torch.Tensor, O: torch.Tensor, F2: torch.Tensor, z: torch.Tensor,
+                     W: torch.Tensor, I_nb: torch.Tensor, theta: float = 5.0, X_next: torch.Tensor | None = None,
+                     F_next: torch.Tensor | None = None, winner: torch.Tensor | None = None,
+                     status: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """TensorMOEA/D selection (Algorithm S.8). ``z`` (float32 ``[m]``) is
+    updated in place to z_min. Returns X_next, F_next, winner (int32 ``[n]``,
+    -1 = kept) and the device status word (int32 ``[1]``)."""
+    n, d = X.shape
+    m = F1.shape[1]
+    T = I_nb.shape[1]
+    dev = X.device
+    X_next = torch.empty_like(X) if X_next is None else X_next
+    F_next = torch.empty_like(F1) if F_next is None else F_next
+    winner = torch.empty(n, dtype=torch.int32, device=dev) if winner is None else winner
+    status = torch.empty(1, dtype=torch.int32, device=dev) if status is None else status
+    nbytes = emo_workspace_size(EMO_OP_MOEAD_SELECT, n, m, T)
+    if nbytes == 0:
+        raise EmoError(1, "emo_workspace_size")
+    ws = _ws(nbytes, ws, dev)
+    _check(lib().emo_moead_select(_ptr(X), _ptr(F1), _ptr(O), _ptr(F2), n, d, m, _ptr(z), _ptr(W), _ptr(I_nb), T,
+                                  float(theta), _ptr(X_next), _ptr(F_next), _ptr(winner), _ptr(status), _ptr(ws),
+                                  nbytes, _stream(stream)), "emo_moead_select")
+    return X_next, F_next, winner, status
 
 
 def _problems(problems) -> ctypes.Array:

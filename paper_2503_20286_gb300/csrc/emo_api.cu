@@ -309,6 +309,7 @@ size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r)
 {
     if (!sizes_ok(n2, m)) return 0;
     if (op == EMO_OP_DOMINANCE) return 0;
+    if (op == EMO_OP_MOEAD_SELECT) return n_r >= 1 && n_r <= n2 ? (size_t)moead_layout(n2, n_r, nullptr, nullptr) : 0;
     int mode = op == EMO_OP_ND_RANK ? MODE_RANK
                : op == EMO_OP_NSGA3_SELECT ? MODE_SELECT
                : op == EMO_OP_HYPE_SELECT ? MODE_HYPE
@@ -360,6 +361,43 @@ emo_status emo_hype_select(const float* F, int64_t n2, int32_t m, const float* v
     ins[0].U = U;
     ins[0].hv_out = hv;
     return run(ins, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+emo_status emo_moead_select(const float* X, const float* F1, const float* O, const float* F2, int64_t n, int64_t d,
+                            int32_t m, float* z, const float* W, const int32_t* I_nb, int32_t T, double theta,
+                            float* X_next, float* F_next, int32_t* winner, int32_t* status_out, void* ws,
+                            size_t ws_bytes, emo_stream_t stream)
+{
+    if (!X || !F1 || !O || !F2 || !z || !W || !I_nb || !X_next || !F_next || !ws) return EMO_ERR_INVALID_ARG;
+    if (!sizes_ok(n, m) || d < 1 || T < 1 || T > n || T > 4096 || !std::isfinite(theta) || theta < 0.0)
+        return EMO_ERR_INVALID_ARG;
+    for (const void* p : {(const void*)X, (const void*)F1, (const void*)O, (const void*)F2, (const void*)z,
+                          (const void*)W, (const void*)I_nb, (const void*)X_next, (const void*)F_next,
+                          (const void*)winner, (const void*)status_out})
+        if (p && !aligned(p, 4)) return EMO_ERR_INVALID_ARG;
+    if (!aligned(ws, 256)) return EMO_ERR_INVALID_ARG;
+    MoeadArgs a;
+    std::memset(&a, 0, sizeof(a));
+    if ((int64_t)ws_bytes < moead_layout(n, T, (char*)ws, &a)) return EMO_ERR_WORKSPACE;
+    DevInfo di = dev_info();
+    if (!di.ok) return EMO_ERR_CUDA;
+    a.X = X;
+    a.F1 = F1;
+    a.O = O;
+    a.F2 = F2;
+    a.W = W;
+    a.I_nb = I_nb;
+    a.z = z;
+    a.X_next = X_next;
+    a.F_next = F_next;
+    a.winner = winner;
+    a.status_out = status_out;
+    a.n = n;
+    a.d = d;
+    a.m = m;
+    a.T = T;
+    a.theta = theta;
+    return launch_moead_select(a, di.sms, (cudaStream_t)stream) == cudaSuccess ? EMO_OK : EMO_ERR_CUDA;
 }
 
 emo_status emo_nsga3_select_ex(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,

@@ -12,5 +12,36 @@ cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, int bl
 // Sticky device status: the first failure any call on this device reported
 // since the last read (k_finish sets it); read after the stream's prior work.
 cudaError_t sticky_status(cudaStream_t s, int32_t* out, bool clear);
+// Folds a call's device status word into the sticky status (stream order).
+cudaError_t sticky_merge(const int32_t* status, cudaStream_t s);
+
+// TensorMOEA/D selection (Algorithm S.8): caller arrays and the workspace
+// regions (status word, z_min keys, per-subproblem best marked value and
+// its lowest offspring index, per-pair marked value).
+struct MoeadArgs {
+    const float* X;
+    const float* F1;
+    const float* O;
+    const float* F2;
+    const float* W;
+    const int32_t* I_nb;
+    float* z;
+    float* X_next;
+    float* F_next;
+    int32_t* winner;
+    int32_t* status_out;
+    int64_t n, d;
+    int32_t m, T;
+    double theta;
+    int32_t* status;
+    uint32_t* zkey;
+    unsigned long long* gmin;
+    int32_t* tie;
+    double* gpair;
+};
+// Workspace bytes of one TensorMOEA/D selection (regions 256-byte aligned);
+// fills the region pointers of `a` when `ws` is given.
+int64_t moead_layout(int64_t n, int32_t T, char* ws, MoeadArgs* a);
+cudaError_t launch_moead_select(const MoeadArgs& a, int sms, cudaStream_t s);
 
 }  // namespace emo

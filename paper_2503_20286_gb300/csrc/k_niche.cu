@@ -425,6 +425,18 @@ cudaError_t sticky_status(cudaStream_t s, int32_t* out, bool clear)
     return e;
 }
 
+__global__ void k_sticky_merge(const int32_t* status)
+{
+    const int32_t st = *status;
+    if (st != 0) atomicCAS(&g_sticky_status, 0, st);
+}
+
+cudaError_t sticky_merge(const int32_t* status, cudaStream_t s)
+{
+    k_sticky_merge<<<1, 1, 0, s>>>(status);
+    return cudaGetLastError();
+}
+
 // Survivors (ascending indices of P and the picked members), the info block
 // and the optional intermediates.
 __global__ void __launch_bounds__(kCoopThreads, 1) k_finish(Plan* plan)

@@ -156,6 +156,29 @@ def moead_neighbours(W: np.ndarray, t: int) -> np.ndarray:
     return out
 
 
+def moead_neighbours_fast(W: np.ndarray, t: int, extra: int = 16) -> np.ndarray:
+    """``moead_neighbours`` for large weight sets: k-d tree candidates, then
+    the same (distance, index) order. A row whose t-th distance ties the
+    last candidate's is recomputed exhaustively, so the result equals the
+    exhaustive definition."""
+    from scipy.spatial import cKDTree
+    Wd = np.asarray(W, dtype=np.float64)
+    n = Wd.shape[0]
+    k = min(n, t + extra)
+    _, cand = cKDTree(Wd).query(Wd, k=k)
+    cand = np.asarray(cand, dtype=np.int64).reshape(n, k)
+    d2 = np.sum((Wd[cand] - Wd[:, None, :]) ** 2, axis=2)
+    out = np.empty((n, t), dtype=np.int32)
+    for i in range(n):
+        order = np.lexsort((cand[i], d2[i]))
+        if k < n and d2[i, order[t - 1]] >= d2[i, order[k - 1]]:
+            full = np.sum((Wd - Wd[i]) ** 2, axis=1)
+            out[i] = np.lexsort((np.arange(n), full))[:t]
+        else:
+            out[i] = cand[i, order[:t]]
+    return out
+
+
 def das_dennis_count(h: int, m: int) -> int:
     return math.comb(h + m - 1, m - 1)
 

@@ -75,3 +75,19 @@ def test_host_argument_checks_reject_before_launch(lib):
     assert L.emo_workspace_size(7, 10, 3, 5) == 0
     assert L.emo_workspace_size(0, 10, 3, 5) == 0    # dominance needs no workspace
     assert L.emo_workspace_status(None, None, None) == 1
+    # TensorMOEA/D selection: X, F1, O, F2, n, d, m, z, W, I_nb, T, theta, X_next, F_next, winner, status, ws
+    mo = lambda n, d, m, T, theta, ws, nbytes: L.emo_moead_select(p, p, p, p, n, d, m, p, p, p, T, theta, p, p,
+                                                                 None, None, ws, nbytes, None)
+    assert L.emo_moead_select(None, p, p, p, 10, 4, 3, p, p, p, 2, 5.0, p, p, None, None, p, 1 << 20, None) == 1
+    assert mo(10, 4, 3, 11, 5.0, p, 1 << 20) == 1                       # T > n
+    assert mo(10, 4, 3, 0, 5.0, p, 1 << 20) == 1                        # T = 0
+    assert mo(10, 0, 3, 2, 5.0, p, 1 << 20) == 1                        # d = 0
+    assert mo(10, 4, 17, 2, 5.0, p, 1 << 20) == 1                       # m > 16
+    assert mo(10, 4, 3, 2, -1.0, p, 1 << 20) == 1                       # theta < 0
+    assert mo(10, 4, 3, 2, float("nan"), p, 1 << 20) == 1               # theta NaN
+    assert mo(10, 4, 3, 2, 5.0, ctypes.c_void_p(128), 1 << 20) == 1     # workspace not 256-byte aligned
+    assert mo(100, 4, 3, 10, 5.0, p, 9983) == 3                         # one byte short
+    # regions: status + z_min keys (256), best value 8n, lowest index 4n, pair values 8nT, each 256-aligned
+    assert L.emo_workspace_size(4, 100, 3, 10) == 9984
+    assert L.emo_workspace_size(4, 100, 3, 0) == 0
+    assert L.emo_workspace_size(4, 100, 3, 101) == 0

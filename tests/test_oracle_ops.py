@@ -343,6 +343,12 @@ def test_neighbours_are_nearest_weights():
         assert inside <= outside
 
 
+def test_fast_neighbours_equal_the_exhaustive_definition():
+    for h, m, t in ((12, 3, 10), (30, 3, 20), (8, 5, 15), (4, 8, 30)):
+        W = wl.das_dennis(h, m)
+        assert np.array_equal(wl.moead_neighbours_fast(W, t), wl.moead_neighbours(W, t))
+
+
 # ------------------------------------------------------------------ IGD
 
 def test_igd_closed_forms():
