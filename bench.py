@@ -131,6 +131,9 @@ DOM_TRAFFIC_SOURCES_SHA1 = "fa9fd63e7add6dad875405f3e2d2091b187c64c6"
 DOM_SOURCES = ("k_dominance.cu", "emo_kernels.cuh", "emo_internal.cuh")
 
 
+FP64_NOMINAL_TFLOPS = 1.25
+
+
 def dom_sources_sha1() -> str:
     import hashlib
     h = hashlib.sha1()
@@ -267,13 +270,20 @@ def moead_timing(emo, torch, dev, flush, stream, steps, h: int = 631, m: int = 3
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
     if int(st.item()) != 0:
-        raise SystemExit("TensorMOEA/D selection failed on the device")
+        raise RuntimeError(f"TensorMOEA/D selection status {int(st.item())} on the device")
     tm = statistics.mean(ms)
     # bytes the selection must move: the taken rows of X or O and X_next, F1, F2, W, F_next, I_nb
     nbytes = 2 * n * d * 4 + 4 * n * m * 4 + n * t * 4
+    # FP64 operations the decisions need: two PBI values per (offspring, neighbour) pair, each
+    # 11 m + 5 (sums of squares and products, m + 1 divisions, two square roots, counted as one each)
+    flops = 2 * n * t * (11 * m + 5)
     return {"selection": "TensorMOEA/D (Algorithm S.8), PBI theta = 5", "subproblems": n, "m": m, "d": d,
             "neighbours": t, "steps": steps, "ms_per_step": tm, "selections_per_s": 1e3 / tm,
-            "replaced": int((win >= 0).sum().item()), "algorithmic_bytes": nbytes}
+            "replaced": int((win >= 0).sum().item()), "algorithmic_bytes": nbytes, "fp64_flops": flops,
+            "roofline": {"bound": "fp64", "achieved": flops / (tm / 1e3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops / (tm / 1e3) / 1e12 / FP64_NOMINAL_TFLOPS,
+                         "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                         "hbm_gbs": nbytes / (tm / 1e3) / 1e9}}
 
 
 def batched_vs_plain(emo, torch, dev, rounds: int = 5):
@@ -500,6 +510,10 @@ def main():
         line["oneshot"] = oneshot_timing(emo, torch, Ft, Rt, n_keep, seed, ws, flush, stream, max(3, args.steps // 2))
         del ws  # the HypE workspace replaces it
         line["hype"] = hype_timing(emo, torch, Ft, F, n_keep, flush, stream, max(3, args.steps // 2))
+        try:
+            line["moead"] = moead_timing(emo, torch, dev, flush, stream, max(3, args.steps // 2))
+        except Exception as e:  # reported in the line; the selection numbers above stand
+            line["moead"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and not args.no_batch:
         line["batched_vs_plain"] = batched_vs_plain(emo, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
