@@ -94,8 +94,13 @@ typedef enum {
     EMO_OP_ND_RANK = 1,
     EMO_OP_NSGA3_SELECT = 2,
     EMO_OP_HYPE_SELECT = 3,
-    EMO_OP_MOEAD_SELECT = 4 /* emo_workspace_size(EMO_OP_MOEAD_SELECT, n, m, T) */
+    EMO_OP_MOEAD_SELECT = 4, /* emo_workspace_size(EMO_OP_MOEAD_SELECT, n, m, T) */
+    EMO_OP_IGD = 5           /* emo_workspace_size(EMO_OP_IGD, n_ref, m, 0) */
 } emo_op;
+
+/* Front shapes of the stand-in objective functions (emo_standin_objectives). */
+#define EMO_SHAPE_LINEAR 0
+#define EMO_SHAPE_SPHERE 1
 
 /* Bytes of workspace needed by `op` for a population of n2 points with m
  * objectives and n_r reference directions (n_r ignored for ranking). Returns
@@ -257,6 +262,64 @@ emo_status emo_moead_select(const float* X, const float* F1, const float* O, con
                             int32_t m, float* z, const float* W, const int32_t* I_nb, int32_t T, double theta,
                             float* X_next, float* F_next, int32_t* winner, int32_t* status_out, void* ws,
                             size_t ws_bytes, emo_stream_t stream);
+
+/*
+ * Offspring of one generation (Appendix S.I): pair p (0 <= p < ceil(n_off/2))
+ * draws two parents uniformly from the n rows of X, crosses every variable
+ * by SBX with probability p_c per pair (distribution index eta_c), clips to
+ * [lo, hi], mutates each variable with probability p_m by polynomial
+ * mutation (original form, eta_m), clips again and writes its children to
+ * rows p and ceil(n_off/2) + p of X_off (the second when it exists).
+ * Randomness: Philox-4x32-10 keyed by `seed`, counter (row, 0x80000000 |
+ * tag << 24 | slot, generation lo, hi); tag 1 parents (slot 0 / 1, word 1
+ * of slot 0 decides crossover), tag 2 SBX spread (slot = variable), tag 3
+ * mutation (slot = variable; word 0 decides, word 1 is mu); a word x is the
+ * uniform x 2^-32 and the index (x n) >> 32. FP64 arithmetic, rounded to
+ * float once. X, X_off device float; lo, hi device float [d] (each
+ * lo < hi), or both NULL for [0, 1]; parents device int32
+ * [ceil(n_off/2)][2] or NULL. d < 2^24.
+ */
+emo_status emo_variation(const float* X, int64_t n, int64_t d, const float* lo, const float* hi, int64_t n_off,
+                         uint64_t seed, uint64_t generation, double eta_c, double eta_m, double p_c, double p_m,
+                         float* X_off, int32_t* parents, emo_stream_t stream);
+
+/*
+ * Stand-in objectives with the front shapes of DTLZ1 / DTLZ2 (the DTLZ
+ * definitions themselves are not part of this library): for decision
+ * vectors x in [0,1]^d (d >= m), g = sum_{i >= m-1} (x_i - 0.5)^2;
+ * EMO_SHAPE_LINEAR: f = 0.5 (1 + 100 g) s with s the stick-breaking simplex
+ * point of x_0 .. x_{m-2} (sum f = 0.5 when g = 0); EMO_SHAPE_SPHERE:
+ * f = (1 + g) u with u the unit vector of angles x_i pi / 2 (||f|| = 1 when
+ * g = 0). FP64, rounded to float once. X device float [n][d], F device
+ * float [n][m].
+ */
+emo_status emo_standin_objectives(const float* X, int64_t n, int64_t d, int32_t m, int32_t shape, float* F,
+                                  emo_stream_t stream);
+
+/*
+ * Inverted generational distance: the mean over the n_ref points of `Ref`
+ * of the distance to the nearest of the n points of F (squared distances in
+ * float, square roots and the sum in double, summed in index order). F, Ref
+ * device float [.][m]; igd_out device double; ws of
+ * emo_workspace_size(EMO_OP_IGD, n_ref, m, 0) bytes (8-byte aligned).
+ */
+emo_status emo_igd(const float* F, int64_t n, int32_t m, const float* Ref, int64_t n_ref, double* igd_out, void* ws,
+                   size_t ws_bytes, emo_stream_t stream);
+
+/*
+ * One NSGA-III generation in place on the device, in stream order (and so
+ * capturable in a CUDA graph): N offspring of (X, F) by emo_variation
+ * (bounds [0, 1]), their stand-in objectives (`shape`), the merged
+ * population of 2N points, emo_nsga3_select_ex (keep N, `niche_mode`,
+ * `seed`, `generation`), and the survivors' rows gathered back into X
+ * [N][d] and F [N][m]. ws of emo_generation_workspace_size(N, d, m, n_r)
+ * bytes, 256-byte aligned; info as for emo_nsga3_select. m <= d <= 2^20.
+ */
+size_t emo_generation_workspace_size(int64_t n, int64_t d, int32_t m, int32_t n_r);
+emo_status emo_nsga3_generation(float* X, float* F, int64_t n, int64_t d, int32_t m, const float* R, int32_t n_r,
+                                int32_t shape, uint64_t seed, uint64_t generation, double eta_c, double eta_m,
+                                double p_c, double p_m, int32_t niche_mode, emo_select_info* info, void* ws,
+                                size_t ws_bytes, emo_stream_t stream);
 
 /*
  * emo_nsga3_select without a caller workspace, for callers that cannot

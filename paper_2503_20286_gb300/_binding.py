@@ -19,7 +19,8 @@ from . import build as _build
 EMO_OK = 0
 STATUS_NAMES = {0: "EMO_OK", 1: "EMO_ERR_INVALID_ARG", 2: "EMO_ERR_NONFINITE", 3: "EMO_ERR_WORKSPACE",
                 4: "EMO_ERR_CUDA", 5: "EMO_ERR_TIMEOUT", 6: "EMO_ERR_NOT_IMPLEMENTED"}
-EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT, EMO_OP_HYPE_SELECT, EMO_OP_MOEAD_SELECT = 0, 1, 2, 3, 4
+EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT, EMO_OP_HYPE_SELECT, EMO_OP_MOEAD_SELECT, EMO_OP_IGD = range(6)
+EMO_SHAPE_LINEAR, EMO_SHAPE_SPHERE = 0, 1
 EMO_NOT_RANKED = 2147483647
 EMO_NICHE_EXACT, EMO_NICHE_ONESHOT = 0, 1
 EMO_MAX_BATCH = 128
@@ -85,6 +86,18 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             L.emo_moead_select.restype = ctypes.c_int
             L.emo_moead_select.argtypes = [vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, i32, ctypes.c_double,
                                            vp, vp, vp, vp, vp, sz, vp]
+            dbl = ctypes.c_double
+            L.emo_variation.restype = ctypes.c_int
+            L.emo_variation.argtypes = [vp, i64, i64, vp, vp, i64, u64, u64, dbl, dbl, dbl, dbl, vp, vp, vp]
+            L.emo_standin_objectives.restype = ctypes.c_int
+            L.emo_standin_objectives.argtypes = [vp, i64, i64, i32, i32, vp, vp]
+            L.emo_igd.restype = ctypes.c_int
+            L.emo_igd.argtypes = [vp, i64, i32, vp, i64, vp, vp, sz, vp]
+            L.emo_generation_workspace_size.restype = sz
+            L.emo_generation_workspace_size.argtypes = [i64, i64, i32, i32]
+            L.emo_nsga3_generation.restype = ctypes.c_int
+            L.emo_nsga3_generation.argtypes = [vp, vp, i64, i64, i32, vp, i32, i32, u64, u64, dbl, dbl, dbl, dbl,
+                                               i32, vp, vp, sz, vp]
             L.emo_autotune.restype = ctypes.c_int
             L.emo_autotune.argtypes = [i32, i64, ctypes.c_char_p]
             L.emo_get_last_device_status.restype = ctypes.c_int
@@ -267,6 +280,65 @@ def emo_moead_select(X: torch.Tensor, F1: torch.Tensor, O: torch.Tensor, F2: tor
                                   float(theta), _ptr(X_next), _ptr(F_next), _ptr(winner), _ptr(status), _ptr(ws),
                                   nbytes, _stream(stream)), "emo_moead_select")
     return X_next, F_next, winner, status
+
+
+def emo_variation(X: torch.Tensor, n_off: int, seed: int, generation: int, eta_c: float = 20.0,
+                  eta_m: float = 20.0, p_c: float = 1.0, p_m: float | None = None, lo: torch.Tensor | None = None,
+                  hi: torch.Tensor | None = None, X_off: torch.Tensor | None = None,
+                  parents: torch.Tensor | None = None, stream=None):
+    """Offspring of one generation (random mating, SBX, PM); bounds [0, 1]
+    unless ``lo``/``hi`` are given; ``p_m`` defaults to 1/D."""
+    n, d = X.shape
+    p_m = 1.0 / d if p_m is None else p_m
+    X_off = torch.empty(n_off, d, dtype=torch.float32, device=X.device) if X_off is None else X_off
+    _check(lib().emo_variation(_ptr(X), n, d, _ptr(lo), _ptr(hi), n_off, seed & 0xFFFFFFFFFFFFFFFF,
+                               generation & 0xFFFFFFFFFFFFFFFF, float(eta_c), float(eta_m), float(p_c), float(p_m),
+                               _ptr(X_off), _ptr(parents), _stream(stream)), "emo_variation")
+    return X_off
+
+
+def emo_standin_objectives(X: torch.Tensor, m: int, shape: int, F: torch.Tensor | None = None, stream=None):
+    """Stand-in objectives of decision vectors X (EMO_SHAPE_LINEAR / _SPHERE)."""
+    n, d = X.shape
+    F = torch.empty(n, m, dtype=torch.float32, device=X.device) if F is None else F
+    _check(lib().emo_standin_objectives(_ptr(X), n, d, m, shape, _ptr(F), _stream(stream)),
+           "emo_standin_objectives")
+    return F
+
+
+def emo_igd(F: torch.Tensor, Ref: torch.Tensor, out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    """IGD of population F to the front Ref (float64 scalar tensor on the device)."""
+    n, m = F.shape
+    out = torch.empty(1, dtype=torch.float64, device=F.device) if out is None else out
+    nbytes = emo_workspace_size(EMO_OP_IGD, Ref.shape[0], m, 0)
+    ws = _ws(nbytes, ws, F.device)
+    _check(lib().emo_igd(_ptr(F), n, m, _ptr(Ref), Ref.shape[0], _ptr(out), _ptr(ws), nbytes, _stream(stream)),
+           "emo_igd")
+    return out
+
+
+def emo_generation_workspace_size(n: int, d: int, m: int, n_r: int) -> int:
+    return int(lib().emo_generation_workspace_size(n, d, m, n_r))
+
+
+def emo_nsga3_generation(X: torch.Tensor, F: torch.Tensor, R: torch.Tensor, shape: int, seed: int, generation: int,
+                         eta_c: float = 20.0, eta_m: float = 20.0, p_c: float = 1.0, p_m: float | None = None,
+                         niche_mode: int = EMO_NICHE_EXACT, info: torch.Tensor | None = None,
+                         ws: torch.Tensor | None = None, stream=None):
+    """One NSGA-III generation in place on (X [N, d], F [N, m])."""
+    n, d = X.shape
+    m = F.shape[1]
+    p_m = 1.0 / d if p_m is None else p_m
+    nbytes = emo_generation_workspace_size(n, d, m, R.shape[0])
+    if nbytes == 0:
+        raise EmoError(1, "emo_generation_workspace_size")
+    ws = _ws(nbytes, ws, X.device)
+    _check(lib().emo_nsga3_generation(_ptr(X), _ptr(F), n, d, m, _ptr(R), R.shape[0], shape,
+                                      seed & 0xFFFFFFFFFFFFFFFF, generation & 0xFFFFFFFFFFFFFFFF, float(eta_c),
+                                      float(eta_m), float(p_c), float(p_m), niche_mode, _ptr(info), _ptr(ws),
+                                      nbytes, _stream(stream)), "emo_nsga3_generation")
+    return X, F
 
 
 def _problems(problems) -> ctypes.Array:

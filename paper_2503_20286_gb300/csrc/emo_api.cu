@@ -305,11 +305,34 @@ emo_status check_select_args(const float* F, int64_t n2, int32_t m, const float*
 
 extern "C" {
 
+// Workspace of one generation: the merged decision vectors and objectives
+// (2N rows), the survivor indices and the selection workspace. Returns the
+// total bytes (0 when the sizes are out of range); fills `at` when given.
+struct GenLayout {
+    int64_t x2, f2, surv, sel, sel_bytes;
+};
+static size_t generation_layout(int64_t n, int32_t m, int32_t n_r, int64_t d, GenLayout* at)
+{
+    auto up = [](int64_t b) { return (b + 255) / 256 * 256; };
+    if (n < 1 || !sizes_ok(2 * n, m) || n_r < 1 || d < m || d > (1 << 20)) return 0;
+    const size_t sel = emo_workspace_size(EMO_OP_NSGA3_SELECT, 2 * n, m, n_r);
+    if (sel == 0) return 0;
+    GenLayout L;
+    L.x2 = 0;
+    L.f2 = up(8 * n * d);
+    L.surv = up(L.f2 + 8 * n * m);
+    L.sel = up(L.surv + 4 * n);
+    L.sel_bytes = (int64_t)sel;
+    if (at) *at = L;
+    return (size_t)(L.sel + L.sel_bytes);
+}
+
 size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r)
 {
     if (!sizes_ok(n2, m)) return 0;
     if (op == EMO_OP_DOMINANCE) return 0;
     if (op == EMO_OP_MOEAD_SELECT) return n_r >= 1 && n_r <= n2 ? (size_t)moead_layout(n2, n_r, nullptr, nullptr) : 0;
+    if (op == EMO_OP_IGD) return (size_t)(n2 * 8);
     int mode = op == EMO_OP_ND_RANK ? MODE_RANK
                : op == EMO_OP_NSGA3_SELECT ? MODE_SELECT
                : op == EMO_OP_HYPE_SELECT ? MODE_HYPE
@@ -398,6 +421,85 @@ emo_status emo_moead_select(const float* X, const float* F1, const float* O, con
     a.T = T;
     a.theta = theta;
     return launch_moead_select(a, di.sms, (cudaStream_t)stream) == cudaSuccess ? EMO_OK : EMO_ERR_CUDA;
+}
+
+size_t emo_generation_workspace_size(int64_t n, int64_t d, int32_t m, int32_t n_r)
+{
+    return generation_layout(n, m, n_r, d, nullptr);
+}
+
+emo_status emo_variation(const float* X, int64_t n, int64_t d, const float* lo, const float* hi, int64_t n_off,
+                         uint64_t seed, uint64_t generation, double eta_c, double eta_m, double p_c, double p_m,
+                         float* X_off, int32_t* parents, emo_stream_t stream)
+{
+    if (!X || !X_off || (!lo) != (!hi) || n < 1 || n > INT32_MAX || d < 1 || d > 0x00FFFFFF || n_off < 1 ||
+        n_off > INT32_MAX || !(eta_c >= 0.0) || !(eta_m >= 0.0) || !std::isfinite(eta_c) || !std::isfinite(eta_m) ||
+        std::isnan(p_c) || std::isnan(p_m))
+        return EMO_ERR_INVALID_ARG;
+    for (const void* p : {(const void*)X, (const void*)lo, (const void*)hi, (const void*)X_off, (const void*)parents})
+        if (p && !aligned(p, 4)) return EMO_ERR_INVALID_ARG;
+    DevInfo di = dev_info();
+    if (!di.ok) return EMO_ERR_CUDA;
+    VariationArgs a{X, lo, hi, X_off, parents, n, d, n_off, seed, generation, eta_c, eta_m, p_c, p_m};
+    return launch_variation(a, di.sms, (cudaStream_t)stream) == cudaSuccess ? EMO_OK : EMO_ERR_CUDA;
+}
+
+emo_status emo_standin_objectives(const float* X, int64_t n, int64_t d, int32_t m, int32_t shape, float* F,
+                                  emo_stream_t stream)
+{
+    if (!X || !F || n < 1 || m < 2 || m > kMaxM || d < m || (shape != EMO_SHAPE_LINEAR && shape != EMO_SHAPE_SPHERE))
+        return EMO_ERR_INVALID_ARG;
+    if (!aligned(X, 4) || !aligned(F, 4)) return EMO_ERR_INVALID_ARG;
+    DevInfo di = dev_info();
+    if (!di.ok) return EMO_ERR_CUDA;
+    return launch_standin(X, n, d, m, shape, F, di.sms, (cudaStream_t)stream) == cudaSuccess ? EMO_OK : EMO_ERR_CUDA;
+}
+
+emo_status emo_igd(const float* F, int64_t n, int32_t m, const float* Ref, int64_t n_ref, double* igd_out, void* ws,
+                   size_t ws_bytes, emo_stream_t stream)
+{
+    if (!F || !Ref || !igd_out || !ws || n < 1 || n_ref < 1 || m < 1 || m > kMaxM) return EMO_ERR_INVALID_ARG;
+    if (!aligned(F, 4) || !aligned(Ref, 4) || !aligned(igd_out, 8) || !aligned(ws, 8)) return EMO_ERR_INVALID_ARG;
+    if ((int64_t)ws_bytes < n_ref * 8) return EMO_ERR_WORKSPACE;
+    DevInfo di = dev_info();
+    if (!di.ok) return EMO_ERR_CUDA;
+    return launch_igd(F, n, m, Ref, n_ref, (double*)ws, igd_out, di.sms, (cudaStream_t)stream) == cudaSuccess
+               ? EMO_OK
+               : EMO_ERR_CUDA;
+}
+
+emo_status emo_nsga3_generation(float* X, float* F, int64_t n, int64_t d, int32_t m, const float* R, int32_t n_r,
+                                int32_t shape, uint64_t seed, uint64_t generation, double eta_c, double eta_m,
+                                double p_c, double p_m, int32_t niche_mode, emo_select_info* info, void* ws,
+                                size_t ws_bytes, emo_stream_t stream)
+{
+    if (!X || !F || !R || !ws || d < m || d > (1 << 20) || !aligned(ws, 256)) return EMO_ERR_INVALID_ARG;
+    GenLayout L;
+    const size_t need = generation_layout(n, m, n_r, d, &L);
+    if (need == 0) return EMO_ERR_INVALID_ARG;
+    if (ws_bytes < need) return EMO_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    float* X2 = (float*)(base + L.x2);
+    float* F2 = (float*)(base + L.f2);
+    int32_t* surv = (int32_t*)(base + L.surv);
+    DevInfo di = dev_info();
+    if (!di.ok) return EMO_ERR_CUDA;
+    if (cudaMemcpyAsync(X2, X, (size_t)(n * d) * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(F2, F, (size_t)(n * m) * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return EMO_ERR_CUDA;
+    emo_status st = emo_variation(X, n, d, nullptr, nullptr, n, seed, generation, eta_c, eta_m, p_c, p_m, X2 + n * d,
+                                  nullptr, stream);
+    if (st != EMO_OK) return st;
+    st = emo_standin_objectives(X2 + n * d, n, d, m, shape, F2 + n * m, stream);
+    if (st != EMO_OK) return st;
+    st = emo_nsga3_select_ex(F2, 2 * n, m, R, n_r, n, seed, generation, niche_mode, surv, info, nullptr,
+                             base + L.sel, (size_t)L.sel_bytes, stream);
+    if (st != EMO_OK) return st;
+    if (launch_gather_rows(X2, surv, n, d, X, di.sms, s) != cudaSuccess ||
+        launch_gather_rows(F2, surv, n, m, F, di.sms, s) != cudaSuccess)
+        return EMO_ERR_CUDA;
+    return EMO_OK;
 }
 
 emo_status emo_nsga3_select_ex(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,

@@ -44,4 +44,22 @@ struct MoeadArgs {
 int64_t moead_layout(int64_t n, int32_t T, char* ws, MoeadArgs* a);
 cudaError_t launch_moead_select(const MoeadArgs& a, int sms, cudaStream_t s);
 
+// One generation's offspring (random mating, SBX, PM; Appendix S.I).
+struct VariationArgs {
+    const float* X;
+    const float* lo;
+    const float* hi;
+    float* Xoff;
+    int32_t* parents;
+    int64_t n, d, n_off;
+    uint64_t seed, gen;
+    double eta_c, eta_m, p_c, p_m;
+};
+cudaError_t launch_variation(const VariationArgs& a, int sms, cudaStream_t s);
+cudaError_t launch_standin(const float* X, int64_t n, int64_t d, int m, int shape, float* F, int sms, cudaStream_t s);
+cudaError_t launch_gather_rows(const float* src, const int32_t* idx, int64_t rows, int64_t width, float* dst, int sms,
+                               cudaStream_t s);
+cudaError_t launch_igd(const float* F, int64_t n, int m, const float* Ref, int64_t n_ref, double* dist, double* out,
+                       int sms, cudaStream_t s);
+
 }  // namespace emo

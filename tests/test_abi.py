@@ -91,3 +91,21 @@ def test_host_argument_checks_reject_before_launch(lib):
     assert L.emo_workspace_size(4, 100, 3, 10) == 9984
     assert L.emo_workspace_size(4, 100, 3, 0) == 0
     assert L.emo_workspace_size(4, 100, 3, 101) == 0
+    # generation operators
+    assert L.emo_variation(None, 10, 4, None, None, 10, 0, 0, 20.0, 20.0, 1.0, 0.25, p, None, None) == 1
+    assert L.emo_variation(p, 10, 4, p, None, 10, 0, 0, 20.0, 20.0, 1.0, 0.25, p, None, None) == 1   # lo without hi
+    assert L.emo_variation(p, 10, 4, None, None, 0, 0, 0, 20.0, 20.0, 1.0, 0.25, p, None, None) == 1  # no offspring
+    assert L.emo_variation(p, 10, 4, None, None, 10, 0, 0, -1.0, 20.0, 1.0, 0.25, p, None, None) == 1  # eta_c < 0
+    assert L.emo_variation(p, 10, 1 << 24, None, None, 10, 0, 0, 20.0, 20.0, 1.0, 0.25, p, None, None) == 1
+    assert L.emo_standin_objectives(p, 10, 2, 3, 1, p, None) == 1                        # d < m
+    assert L.emo_standin_objectives(p, 10, 12, 3, 7, p, None) == 1                       # unknown shape
+    assert L.emo_igd(p, 10, 3, p, 5, p, p, 39, None) == 3                                 # 8 bytes per reference
+    assert L.emo_igd(p, 10, 3, p, 0, p, p, 1 << 20, None) == 1
+    assert L.emo_workspace_size(5, 1000, 3, 0) == 8000
+    assert L.emo_generation_workspace_size(100, 2, 3, 91) == 0                            # d < m
+    assert L.emo_generation_workspace_size(100, 12, 3, 0) == 0                            # no directions
+    assert L.emo_generation_workspace_size(100, (1 << 20) + 1, 3, 91) == 0
+    assert L.emo_nsga3_generation(p, p, 100, 2, 3, p, 91, 1, 0, 0, 20.0, 20.0, 1.0, 0.1, 0, None, p, 1 << 30,
+                                  None) == 1                                              # d < m
+    assert L.emo_nsga3_generation(p, p, 100, 12, 3, p, 91, 1, 0, 0, 20.0, 20.0, 1.0, 0.1, 0, None,
+                                  ctypes.c_void_p(128), 1 << 30, None) == 1               # workspace alignment
