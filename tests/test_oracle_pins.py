@@ -463,3 +463,45 @@ def test_hype_selection_invariants(case):
     kept = np.setdiff1d(surv, np.flatnonzero(r < l))
     if len(last) and len(kept):   # every kept last-front point scores at least every dropped one
         assert vhv[kept].min() >= vhv[last].max()
+
+
+def _layering_2d(F):
+    """Textbook two-objective non-dominated sorting: visit the points in
+    lexicographic order (f1, then f2); a point joins the first front whose
+    most recent member does not dominate it. The most recent member of a
+    front has that front's smallest f2 among points with f1 <= the visited
+    point's f1, so it is the only member that can dominate the point, and
+    the fronts' most recent f2 values grow with the front index (binary
+    search)."""
+    order = sorted(range(len(F)), key=lambda i: (float(F[i][0]), float(F[i][1]), i))
+    last = []                        # most recent member of each front
+    rank = np.zeros(len(F), np.int32)
+
+    def dominates(a, b):
+        return a[0] <= b[0] and a[1] <= b[1] and (a[0] < b[0] or a[1] < b[1])
+
+    for i in order:
+        lo, hi = 0, len(last)
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if dominates(F[last[mid]], F[i]):
+                lo = mid + 1
+            else:
+                hi = mid
+        if lo == len(last):
+            last.append(i)
+        else:
+            last[lo] = i
+        rank[i] = lo
+    return rank
+
+
+@pytest.mark.parametrize("seed,q", [(1, 4), (2, 16), (3, 0)])
+def test_two_objective_ranks_equal_textbook_layering(seed, q):
+    rng = np.random.default_rng(seed)
+    F = rng.random((600, 2)).astype(np.float32)
+    if q:
+        F = (np.round(F * q) / q).astype(np.float32)     # ties and duplicates
+    ref = _layering_2d(F)
+    assert np.array_equal(oracle.nd_sort_deb(F), ref)
+    assert np.array_equal(oracle.nd_sort_peel(F), ref)
