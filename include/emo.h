@@ -256,7 +256,8 @@ emo_status emo_hype_select(const float* F, int64_t n2, int32_t m, const float* v
  * marked j and F1_j otherwise. PBI: d1 = |(f - z).w| / ||w||,
  * d2 = ||(f - z) - d1 w / ||w|| ||, g = d1 + theta d2, in FP64 from the
  * float inputs (k ascending, no contraction). Asynchronous on `stream`;
- * argument errors are returned at once. 2 <= m <= 16, 1 <= T <= min(n, 4096).
+ * argument errors are returned at once. 1 <= n <= 2^21, 2 <= m <= 16,
+ * 1 <= T <= min(n, 4096).
  */
 emo_status emo_moead_select(const float* X, const float* F1, const float* O, const float* F2, int64_t n, int64_t d,
                             int32_t m, float* z, const float* W, const int32_t* I_nb, int32_t T, double theta,
