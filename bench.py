@@ -286,6 +286,37 @@ def moead_timing(emo, torch, dev, flush, stream, steps, h: int = 631, m: int = 3
                          "hbm_gbs": nbytes / (tm / 1e3) / 1e9}}
 
 
+def nd_rank_timing(emo, torch, dev, Ft, n_keep, flush, stream, steps):
+    """Non-dominated sorting alone (emo_nd_rank): the benchmark population
+    down to the last front the selection needs, and the 2N = 20,000 M = 3
+    sphere population ranked completely. Device time per call (CUDA events,
+    L2 flushed before each)."""
+    from paper_2503_20286_gb300 import workloads as wl
+    p1 = wl.config(1)
+    F1 = torch.from_numpy(p1.F).to(dev)
+    out = {}
+    for name, F, keep in (("bench_population_to_last_front", Ft, n_keep), ("n2_20000_all_fronts", F1, 0)):
+        n2, m = F.shape
+        ws = torch.empty(emo.emo_workspace_size(emo.EMO_OP_ND_RANK, n2, m, 0), dtype=torch.uint8, device=dev)
+        rank = torch.empty(n2, dtype=torch.int32, device=dev)
+        last = torch.empty(1, dtype=torch.int32, device=dev)
+        for _ in range(2):
+            emo.emo_nd_rank(F, keep, rank=rank, last_rank=last, ws=ws, stream=stream)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            emo.emo_nd_rank(F, keep, rank=rank, last_rank=last, ws=ws, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = statistics.mean(ms)
+        out[name] = {"n2": n2, "m": m, "ms": t, "pairs_per_s": float(n2) * n2 / (t / 1e3),
+                     "fronts_ranked": int(last.item()) + 1}
+    return out
+
+
 def batched_vs_plain(emo, torch, dev, rounds: int = 5):
     """64 uneven populations: one batched call replayed from a CUDA graph
     versus 64 plain calls on one stream (device time, CUDA events)."""
@@ -331,7 +362,10 @@ def batched_vs_plain(emo, torch, dev, rounds: int = 5):
     e[3].record(stream)
     torch.cuda.synchronize()
     b_ms, p_ms = e[0].elapsed_time(e[1]) / rounds, e[2].elapsed_time(e[3]) / rounds
+    pairs = float(sum(p.n2 * p.n2 for p in probs))
     return {"populations": len(probs), "batched_ms": b_ms, "plain_ms": p_ms, "speedup": p_ms / b_ms,
+            "batched_populations_per_s": len(probs) * 1e3 / b_ms, "batched_pairs_per_s": pairs * 1e3 / b_ms,
+            "plain_populations_per_s": len(probs) * 1e3 / p_ms,
             "batched": "one emo_nsga3_select_batch call replayed from a CUDA graph",
             "plain": "64 emo_nsga3_select calls on one stream", "survivors_identical": bool(ok)}
 
@@ -510,6 +544,10 @@ def main():
         line["oneshot"] = oneshot_timing(emo, torch, Ft, Rt, n_keep, seed, ws, flush, stream, max(3, args.steps // 2))
         del ws  # the HypE workspace replaces it
         line["hype"] = hype_timing(emo, torch, Ft, F, n_keep, flush, stream, max(3, args.steps // 2))
+        try:
+            line["nd_rank"] = nd_rank_timing(emo, torch, dev, Ft, n_keep, flush, stream, max(3, args.steps // 2))
+        except Exception as e:  # reported in the line; the selection numbers above stand
+            line["nd_rank"] = {"error": f"{type(e).__name__}: {e}"}
         try:
             line["moead"] = moead_timing(emo, torch, dev, flush, stream, max(3, args.steps // 2))
         except Exception as e:  # reported in the line; the selection numbers above stand
