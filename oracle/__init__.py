@@ -33,22 +33,41 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "emo_oracle.c")
 _SRCS = [_SRC, os.path.join(_HERE, "emo_oracle_ops.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp = None
 
 NOT_RANKED = np.iinfo(np.int32).max
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction). Returns the .so path."""
-    if (not force and os.path.exists(_LIB_PATH)
-            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src) for src in _SRCS)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+def _compile(path: str, extra: list[str], force: bool) -> str:
+    if (not force and os.path.exists(path)
+            and all(os.path.getmtime(path) >= os.path.getmtime(src) for src in _SRCS)):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", *extra,
                            *_SRCS, "-o", tmp, "-lm"])
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction): the single-threaded
+    library and, where the compiler has OpenMP, the all-core build of the
+    same source (``liboracle_omp.so``). Returns the single-threaded path."""
+    path = _compile(_LIB_PATH, [], force)
+    try:
+        _compile(_OMP_PATH, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass  # no OpenMP runtime: only the single-threaded oracle exists
+    return path
+
+
+def has_parallel() -> bool:
+    """True when the all-core build of the oracle is available."""
+    build()
+    return os.path.exists(_OMP_PATH)
 
 
 class _Trace(ctypes.Structure):
@@ -60,55 +79,76 @@ class _Trace(ctypes.Structure):
                 ("n_levels", ctypes.c_int32), ("near_ties", ctypes.c_int32)]
 
 
-def lib():
-    global _lib
+def lib(parallel: bool = False):
+    """The single-threaded oracle library, or with ``parallel`` its all-core
+    build (same source and arithmetic, OpenMP over points)."""
+    global _lib, _omp
     with _lock:
+        if parallel:
+            if _omp is None:
+                build()
+                if not os.path.exists(_OMP_PATH):
+                    raise OracleError("the all-core oracle needs gcc with OpenMP")
+                _omp = _declare(ctypes.CDLL(_OMP_PATH))
+            return _omp
         if _lib is None:
-            _lib = ctypes.CDLL(build())
-            _lib.oracle_nd_sort_deb.restype = ctypes.c_int64
-            _lib.oracle_nd_sort_peel.restype = ctypes.c_int64
-            _lib.oracle_nsga3_select.restype = ctypes.c_int
-            _lib.oracle_nsga3_select.argtypes = [
-                ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32,
-                ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
-                ctypes.POINTER(_Trace)]
-            _lib.oracle_hype_select.restype = ctypes.c_int
-            _lib.oracle_hype_select.argtypes = [
-                ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
-                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-            _lib.oracle_nsga3_select_mode.restype = ctypes.c_int
-            _lib.oracle_nsga3_select_mode.argtypes = [
-                ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32,
-                ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
-                ctypes.POINTER(_Trace)]
-            _lib.oracle_dominance_bits.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
-                                                   ctypes.c_void_p, ctypes.c_int64]
-            _lib.oracle_domination_counts.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
-                                                      ctypes.c_void_p]
-            _lib.oracle_nd_sort_deb.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
-                                                ctypes.c_void_p]
-            _lib.oracle_nd_sort_peel.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
-                                                 ctypes.c_void_p]
-            _lib.oracle_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-            _lib.oracle_dominates.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
-            vp, i64, dbl, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
-            _lib.oracle_sbx_pair.restype = None
-            _lib.oracle_sbx_pair.argtypes = [dbl, dbl, dbl, dbl, vp, vp]
-            _lib.oracle_pm_value.restype = dbl
-            _lib.oracle_pm_value.argtypes = [dbl, dbl, dbl, dbl, dbl]
-            _lib.oracle_variation.restype = ctypes.c_int
-            _lib.oracle_variation.argtypes = [vp, i64, i64, vp, vp, i64, u64, u64, dbl, dbl, dbl, dbl, vp, vp]
-            _lib.oracle_pbi.restype = dbl
-            _lib.oracle_pbi.argtypes = [vp, vp, vp, ctypes.c_int, dbl]
-            _lib.oracle_moead_select.restype = ctypes.c_int
-            _lib.oracle_moead_select.argtypes = [vp, vp, vp, vp, i64, i64, ctypes.c_int, vp, vp, vp,
-                                                 ctypes.c_int32, dbl, vp, vp, vp]
-            _lib.oracle_moead_offspring.restype = ctypes.c_int
-            _lib.oracle_moead_offspring.argtypes = [vp, i64, i64, vp, vp, vp, ctypes.c_int32, u64, u64,
-                                                    dbl, dbl, dbl, vp, vp]
-            _lib.oracle_igd.restype = dbl
-            _lib.oracle_igd.argtypes = [vp, i64, ctypes.c_int, vp, i64]
+            _lib = _declare(ctypes.CDLL(build()))
         return _lib
+
+
+def _declare(_lib):
+    """Argument and return types of the exported oracle routines."""
+    _lib.oracle_nd_sort_deb.restype = ctypes.c_int64
+    _lib.oracle_nd_sort_peel.restype = ctypes.c_int64
+    _lib.oracle_nsga3_select.restype = ctypes.c_int
+    _lib.oracle_nsga3_select.argtypes = [
+        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32,
+        ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+        ctypes.POINTER(_Trace)]
+    _lib.oracle_hype_select.restype = ctypes.c_int
+    _lib.oracle_hype_select.argtypes = [
+        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+        ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    _lib.oracle_nsga3_select_mode.restype = ctypes.c_int
+    _lib.oracle_nsga3_select_mode.argtypes = [
+        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int32,
+        ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
+        ctypes.POINTER(_Trace)]
+    _lib.oracle_dominance_bits.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_int64]
+    _lib.oracle_domination_counts.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.c_void_p]
+    _lib.oracle_nd_sort_deb.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_void_p]
+    _lib.oracle_nd_sort_peel.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                         ctypes.c_void_p]
+    _lib.oracle_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    _lib.oracle_dominates.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    vp, i64, dbl, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+    _lib.oracle_sbx_pair.restype = None
+    _lib.oracle_sbx_pair.argtypes = [dbl, dbl, dbl, dbl, vp, vp]
+    _lib.oracle_pm_value.restype = dbl
+    _lib.oracle_pm_value.argtypes = [dbl, dbl, dbl, dbl, dbl]
+    _lib.oracle_variation.restype = ctypes.c_int
+    _lib.oracle_variation.argtypes = [vp, i64, i64, vp, vp, i64, u64, u64, dbl, dbl, dbl, dbl, vp, vp]
+    _lib.oracle_pbi.restype = dbl
+    _lib.oracle_pbi.argtypes = [vp, vp, vp, ctypes.c_int, dbl]
+    _lib.oracle_moead_select.restype = ctypes.c_int
+    _lib.oracle_moead_select.argtypes = [vp, vp, vp, vp, i64, i64, ctypes.c_int, vp, vp, vp,
+                                         ctypes.c_int32, dbl, vp, vp, vp]
+    _lib.oracle_moead_offspring.restype = ctypes.c_int
+    _lib.oracle_moead_offspring.argtypes = [vp, i64, i64, vp, vp, vp, ctypes.c_int32, u64, u64,
+                                            dbl, dbl, dbl, vp, vp]
+    _lib.oracle_igd.restype = dbl
+    _lib.oracle_igd.argtypes = [vp, i64, ctypes.c_int, vp, i64]
+    _lib.oracle_threads.restype = ctypes.c_int
+    _lib.oracle_threads.argtypes = [ctypes.c_int]
+    return _lib
+
+
+def threads(n: int = 0) -> int:
+    """Sets (n > 0) and returns the thread count of the all-core oracle."""
+    return int(lib(parallel=True).oracle_threads(int(n)))
 
 
 def _f32(F) -> np.ndarray:
@@ -142,10 +182,10 @@ def domination_counts(F) -> np.ndarray:
     return c
 
 
-def nd_sort_deb(F) -> np.ndarray:
+def nd_sort_deb(F, parallel: bool = False) -> np.ndarray:
     F = _f32(F)
     r = np.zeros(F.shape[0], dtype=np.int32)
-    if lib().oracle_nd_sort_deb(_p(F), F.shape[0], F.shape[1], _p(r)) < 0:
+    if lib(parallel).oracle_nd_sort_deb(_p(F), F.shape[0], F.shape[1], _p(r)) < 0:
         raise MemoryError("oracle nd sort")
     return r
 
@@ -175,8 +215,9 @@ NICHE_ONESHOT = 1  # one-shot niche selection of Algorithm S.4 + Update-Rank (Al
 
 
 def nsga3_select(F, R, n_keep: int, seed: int, generation: int = 0, trace: bool = True,
-                 mode: int = NICHE_EXACT):
-    """Survivor indices (ascending) and, with ``trace``, every intermediate."""
+                 mode: int = NICHE_EXACT, parallel: bool = False):
+    """Survivor indices (ascending) and, with ``trace``, every intermediate.
+    ``parallel`` runs the all-core build (identical results)."""
     F = _f32(F)
     R = _f32(R)
     n2, m = F.shape
@@ -192,7 +233,7 @@ def nsga3_select(F, R, n_keep: int, seed: int, generation: int = 0, trace: bool 
                 "picked": np.zeros(n2, np.uint8)}
         for k, v in bufs.items():
             setattr(t, k, _p(v))
-    rc = lib().oracle_nsga3_select_mode(_p(F), n2, m, _p(R), n_r, n_keep,
+    rc = lib(parallel).oracle_nsga3_select_mode(_p(F), n2, m, _p(R), n_r, n_keep,
                                         seed & 0xFFFFFFFFFFFFFFFF, generation & 0xFFFFFFFFFFFFFFFF, int(mode),
                                         _p(surv), ctypes.byref(t))
     if rc != 0:

@@ -53,8 +53,29 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORACLE_NOT_RANKED INT32_MAX
+
+/* The same source builds a single-threaded library and, with -fopenmp, an
+   all-core one. Only two loops run in parallel, each over independent
+   points with no shared writes: the pairwise dominance relation (one row i
+   per iteration) and the association (one point per iteration). Every
+   value is computed by the same operations in the same order either way,
+   so both builds return identical results. Sets the thread count when
+   n > 0 and returns the count in use (1 without OpenMP). */
+int oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ---------------------------------------------------------------------- */
 /* Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random     */
@@ -170,24 +191,27 @@ int64_t oracle_nd_sort_deb(const float* F, int64_t n, int m, int32_t* rank)
     int64_t* nxt = (int64_t*)malloc((size_t)n * sizeof(int64_t));
     if (!S || !cnt || !cur || !nxt) { free(S); free(cnt); free(cur); free(nxt); return -1; }
 
-    /* Each unordered pair is compared once; both relations follow from the
-       per-objective < and > flags (same definition as Listing 1). */
+    /* Row i compares point i with every other point j; both relations
+       follow from the per-objective < and > flags (same definition as
+       Listing 1): i dominates j puts j into S_i, j dominates i counts one
+       dominator of i. Each iteration writes only row i of S and n_i. */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
     for (int64_t i = 0; i < n; ++i) {
-        for (int64_t j = i + 1; j < n; ++j) {
+        int64_t ni = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
             int lt = 0, gt = 0;
             for (int k = 0; k < m; ++k) {
                 double a = (double)F[i * m + k], b = (double)F[j * m + k];
                 if (a < b) lt = 1;
                 else if (a > b) gt = 1;
             }
-            if (lt && !gt) {            /* i dominates j */
-                S[i * words + (j >> 6)] |= 1ull << (j & 63);
-                cnt[j] += 1;
-            } else if (gt && !lt) {     /* j dominates i */
-                S[j * words + (i >> 6)] |= 1ull << (i & 63);
-                cnt[i] += 1;
-            }
+            if (lt && !gt) S[i * words + (j >> 6)] |= 1ull << (j & 63);   /* i dominates j */
+            else if (gt && !lt) ni += 1;                                  /* j dominates i */
         }
+        cnt[i] = ni;
     }
     int64_t ncur = 0;
     for (int64_t i = 0; i < n; ++i) {
@@ -424,8 +448,12 @@ int oracle_nsga3_select_mode(const float* F, int64_t n2, int m, const float* R, 
         for (int k = 0; k < m; ++k) if (a[k] <= 1e-10) a[k] = 1.0;
     }
 
-    /* 7-8. Normalise S and associate each point with the nearest line. */
+    /* 7-8. Normalise S and associate each point with the nearest line
+       (points are independent: each iteration writes only its own row). */
     int32_t near_ties = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : near_ties)
+#endif
     for (int64_t i = 0; i < n2; ++i) {
         pi[i] = -1;
         dist[i] = NAN;

@@ -1,0 +1,48 @@
+"""The all-core oracle build (OpenMP over the rows of the dominance relation
+and over the points of the association) returns exactly what the
+single-threaded build returns: ranks, pi, FP64 distances, normalised
+objectives, niche counts, picks and survivors. It is what writes the
+fixture of the 2N = 400,000 workload, so this equality is what lets that
+fixture stand for the single-threaded oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_20286_gb300 import workloads as wl
+
+pytestmark = pytest.mark.skipif(not oracle.has_parallel(), reason="gcc without OpenMP")
+
+
+def _same(a, b):
+    if isinstance(a, np.ndarray):
+        return np.array_equal(a, b, equal_nan=a.dtype.kind == "f")
+    return a == b
+
+
+def _problems():
+    p0, p1, p2 = wl.config(0), wl.config(1), wl.config(2)
+    F2 = np.ascontiguousarray(p2.F[:20000])
+    return [("workload 0", p0.F, p0.R, p0.n_keep, p0.seed),
+            ("workload 1", p1.F, p1.R, p1.n_keep, p1.seed),
+            ("workload 2, first 20,000 points (1/64 grid, ties)", F2, p2.R, 10000, p2.seed),
+            ("workload 2b, first 20,000 points (nadir fallback)", wl.ideal_corner_case(F2), p2.R, 10000, p2.seed)]
+
+
+@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("mode", [oracle.NICHE_EXACT, oracle.NICHE_ONESHOT])
+def test_parallel_oracle_equals_single_thread(case, mode):
+    name, F, R, n_keep, seed = _problems()[case]
+    oracle.threads(8)
+    s1, t1 = oracle.nsga3_select(F, R, n_keep, seed, 3, mode=mode)
+    s8, t8 = oracle.nsga3_select(F, R, n_keep, seed, 3, mode=mode, parallel=True)
+    assert np.array_equal(s1, s8), name
+    for k in t1:
+        assert _same(t1[k], t8[k]), (name, k)
+
+
+def test_parallel_deb_sort_equals_single_thread_with_ties():
+    rng = np.random.default_rng(5)
+    F = rng.integers(0, 6, size=(3000, 4)).astype(np.float32)
+    oracle.threads(5)
+    assert np.array_equal(oracle.nd_sort_deb(F), oracle.nd_sort_deb(F, parallel=True))
+    assert np.array_equal(oracle.nd_sort_deb(F), oracle.nd_sort_peel(F))
