@@ -277,7 +277,8 @@ emo_status emo_moead_select(const float* X, const float* F1, const float* O, con
  * mutation (slot = variable; word 0 decides, word 1 is mu); a word x is the
  * uniform x 2^-32 and the index (x n) >> 32. FP64 arithmetic, rounded to
  * float once. X, X_off device float; lo, hi device float [d] (each
- * lo < hi), or both NULL for [0, 1]; parents device int32
+ * lo < hi; a variable with hi <= lo is not mutated, so it never turns into
+ * NaN), or both NULL for [0, 1]; parents device int32
  * [ceil(n_off/2)][2] or NULL. d < 2^24.
  */
 emo_status emo_variation(const float* X, int64_t n, int64_t d, const float* lo, const float* hi, int64_t n_off,

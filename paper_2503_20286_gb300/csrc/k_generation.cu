@@ -102,7 +102,9 @@ __global__ void __launch_bounds__(kGenThreads) k_variation(VariationArgs a)
             if (row >= a.n_off) continue;
             double v = clip(c[child], lo, hi);
             const uint4 rm = gen_random(a.seed, a.gen, row, 3u, k);
-            if (hit(rm.x, a.p_m)) v = clip(pm(v, lo, hi, unit_of(rm.y), a.eta_m), lo, hi);
+            // PM is defined over (x - lo) / (hi - lo): a variable without a
+            // positive width (outside the contract) is left unmutated.
+            if (hit(rm.x, a.p_m) && hi > lo) v = clip(pm(v, lo, hi, unit_of(rm.y), a.eta_m), lo, hi);
             a.Xoff[row * a.d + k] = (float)v;
         }
     }

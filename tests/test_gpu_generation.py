@@ -16,7 +16,7 @@ import oracle
 from paper_2503_20286_gb300 import _binding as emo
 from paper_2503_20286_gb300 import workloads as wl
 
-pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="generation kernels: first GPU run pending")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -55,6 +55,18 @@ def test_variation_with_bounds():
     ref, _ = oracle.variation(X, lo, hi, 200, seed=8, generation=1, p_m=0.5)
     got = emo.emo_variation(_dev(X), 200, 8, 1, p_m=0.5, lo=_dev(lo), hi=_dev(hi)).cpu().numpy()
     assert _ulps(got, ref).max() <= 2
+
+
+def test_variation_fixed_variable_stays_finite():
+    # lo == hi is outside the operator's definition (PM divides by hi - lo):
+    # the oracle rejects it; the device leaves that variable at its bound.
+    X = wl.decision_vectors(64, 4, seed=9)
+    X[:, 2] = 0.25
+    lo = np.array([0.0, 0.0, 0.25, 0.0], np.float32)
+    hi = np.array([1.0, 1.0, 0.25, 1.0], np.float32)
+    got = emo.emo_variation(_dev(X), 64, 3, 0, p_m=1.0, lo=_dev(lo), hi=_dev(hi)).cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert np.all(got[:, 2] == np.float32(0.25))
 
 
 @pytest.mark.parametrize("shape,m,d", [("sphere", 3, 12), ("linear", 3, 7), ("sphere", 8, 17), ("linear", 5, 14)])
