@@ -336,7 +336,8 @@ def moead_offspring(X, lo, hi, I_nb, seed: int, generation: int, eta_c: float = 
     return O, parents
 
 
-def igd(F, Ref) -> float:
-    """Inverted generational distance of population F to the front Ref."""
+def igd(F, Ref, parallel: bool = False) -> float:
+    """Inverted generational distance of population F to the front Ref
+    (``parallel``: the all-core build, identical result)."""
     F, Ref = _f32(F), _f32(Ref)
-    return lib().oracle_igd(_p(F), F.shape[0], F.shape[1], _p(Ref), Ref.shape[0])
+    return lib(parallel).oracle_igd(_p(F), F.shape[0], F.shape[1], _p(Ref), Ref.shape[0])

@@ -301,7 +301,13 @@ int oracle_moead_offspring(const float* X, int64_t n, int64_t d, const float* lo
 double oracle_igd(const float* F, int64_t n, int m, const float* Ref, int64_t nref)
 {
     if (!F || !Ref || n < 1 || nref < 1 || m < 1) return NAN;
-    double total = 0.0;
+    double* nearest = (double*)malloc((size_t)nref * sizeof(double));
+    if (!nearest) return NAN;
+    /* the nearest distance of each reference point (independent; the
+       all-core build runs them in parallel), then the sum in index order */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t r = 0; r < nref; ++r) {
         double best = INFINITY;
         for (int64_t i = 0; i < n; ++i) {
@@ -312,7 +318,10 @@ double oracle_igd(const float* F, int64_t n, int m, const float* Ref, int64_t nr
             }
             if (s < best) best = s;
         }
-        total = total + sqrt(best);
+        nearest[r] = sqrt(best);
     }
+    double total = 0.0;
+    for (int64_t r = 0; r < nref; ++r) total = total + nearest[r];
+    free(nearest);
     return total / (double)nref;
 }

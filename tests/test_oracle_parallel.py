@@ -46,3 +46,10 @@ def test_parallel_deb_sort_equals_single_thread_with_ties():
     oracle.threads(5)
     assert np.array_equal(oracle.nd_sort_deb(F), oracle.nd_sort_deb(F, parallel=True))
     assert np.array_equal(oracle.nd_sort_deb(F), oracle.nd_sort_peel(F))
+
+
+def test_parallel_igd_equals_single_thread():
+    F = wl.population(3000, 3, 12, "sphere", seed=4)
+    R = wl.reference_front(60, 3, "sphere")
+    oracle.threads(7)
+    assert oracle.igd(F, R) == oracle.igd(F, R, parallel=True)
