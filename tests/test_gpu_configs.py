@@ -142,3 +142,51 @@ def test_config4_full_size_properties():
         j = int(np.argmin(d2))
         assert g["pi"][i] == j or np.isclose(d2[g["pi"][i]], d2[j], rtol=1e-12, atol=0), (i, g["pi"][i], j)
     np.testing.assert_allclose(g["fnorm"][S[:1000]], ((F64[S[:1000]] - g["z"]) / g["a"]), rtol=1e-5)
+
+
+def _sha(a) -> str:
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def test_config4_bit_exact_against_oracle_fixture():
+    """2N = 400,000 (the benchmark workload) against the oracle's fixture
+    (tests/golden/make_config4_golden.py, written by the all-core oracle):
+    survivors and ranks of S element by element, z, extreme points and FP64
+    intercepts exactly, pi and the FP64 distances over S by SHA-256 (and per
+    chunk, to locate a difference), the sampled pi / distances exactly, the
+    normalised objectives within 1e-5 relative of FP64."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "config4_oracle.npz")
+    gold = np.load(path)
+    p = wl.config(4)
+    assert _sha(p.F.astype("<f4")) == str(gold["F_sha256"]), "the generator produced a different population"
+    assert _sha(p.R.astype("<f4")) == str(gold["R_sha256"])
+    s, info, g = _gpu.gpu_select(p.F, p.R, p.n_keep, p.seed, p.generation, debug=True)
+    assert info["status"] == 0
+    n2 = p.n2
+    assert info["last_rank"] == int(gold["last_rank"])
+    assert info["n_before"] == int(gold["n_before"]) and info["n_last"] == int(gold["n_last"])
+    assert info["fallback_used"] == int(gold["fallback"])
+    mask = np.unpackbits(gold["survivor_mask"], count=n2, bitorder="little").astype(bool)
+    ref_surv = np.flatnonzero(mask)
+    assert np.array_equal(s, ref_surv), (np.setdiff1d(s, ref_surv)[:10], np.setdiff1d(ref_surv, s)[:10])
+    rank_u8 = gold["rank_u8"]
+    S = np.flatnonzero(rank_u8 != 255)
+    assert np.array_equal(g["rank"][S], rank_u8[S].astype(np.int32))
+    assert np.all(g["rank"][rank_u8 == 255] == emo.EMO_NOT_RANKED)
+    assert np.array_equal(g["z"].astype(np.float64), gold["z"])
+    assert np.array_equal(g["extreme"], gold["extreme"])
+    assert np.array_equal(g["a"], gold["a"])
+    si = gold["sample_index"]
+    assert np.array_equal(g["pi"][si], gold["sample_pi"])
+    assert np.array_equal(g["dist"][si], gold["sample_dist"])
+    pi_S, dist_S = g["pi"][S].astype("<i4"), g["dist"][S].astype("<f8")
+    if _sha(pi_S) != str(gold["pi_sha256"]) or _sha(dist_S) != str(gold["dist_sha256"]):
+        bad = [c for c, (a, b, ga, gb) in enumerate(zip(np.array_split(pi_S, 64), np.array_split(dist_S, 64),
+                                                        gold["pi_chunk_sha256"], gold["dist_chunk_sha256"]))
+               if _sha(a) != str(ga) or _sha(b) != str(gb)]
+        raise AssertionError(f"pi / FP64 distances differ from the oracle in chunks {bad} of S (64 chunks)")
+    assert _sha(g["rho"].astype("<i4")) == str(gold["rho_sha256"])
+    fn64 = (p.F[S].astype(np.float64) - gold["z"]) / gold["a"]
+    np.testing.assert_allclose(g["fnorm"][S], fn64, rtol=1e-5, atol=0)
