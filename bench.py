@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-population batched-vs-plain timing")
+    ap.add_argument("--no-parity", action="store_true",
+                    help="skip the per-workload oracle timing and error report of the CPU-baseline leg")
     return ap.parse_args()
 
 
@@ -274,9 +276,10 @@ def moead_timing(emo, torch, dev, flush, stream, steps, h: int = 631, m: int = 3
     tm = statistics.mean(ms)
     # bytes the selection must move: the taken rows of X or O and X_next, F1, F2, W, F_next, I_nb
     nbytes = 2 * n * d * 4 + 4 * n * m * 4 + n * t * 4
-    # FP64 operations the decisions need: two PBI values per (offspring, neighbour) pair, each
-    # 11 m + 5 (sums of squares and products, m + 1 divisions, two square roots, counted as one each)
-    flops = 2 * n * t * (11 * m + 5)
+    # FP64 operations the decisions need, counting a division or square root as one: per
+    # subproblem ||w||, w / ||w|| and its own PBI value (12 m + 6); per (offspring, neighbour)
+    # pair the offspring's PBI value with those reused (8 m + 4: one division, one square root)
+    flops = n * (12 * m + 6) + n * t * (8 * m + 4)
     return {"selection": "TensorMOEA/D (Algorithm S.8), PBI theta = 5", "subproblems": n, "m": m, "d": d,
             "neighbours": t, "steps": steps, "ms_per_step": tm, "selections_per_s": 1e3 / tm,
             "replaced": int((win >= 0).sum().item()), "algorithmic_bytes": nbytes, "fp64_flops": flops,
@@ -368,6 +371,166 @@ def batched_vs_plain(emo, torch, dev, rounds: int = 5):
             "plain_populations_per_s": len(probs) * 1e3 / p_ms,
             "batched": "one emo_nsga3_select_batch call replayed from a CUDA graph",
             "plain": "64 emo_nsga3_select calls on one stream", "survivors_identical": bool(ok)}
+
+
+def generation_loop(emo, torch, dev, flush, stream, gens: int = 20, n: int = N2 // 2, d: int = D_VARS):
+    """The paper-scale NSGA-III run (Appendix S.I operators, Section VI):
+    N = 200,000 decision vectors in [0, 1)^12 on the sphere-front stand-in,
+    200,028 Das-Dennis directions (H = 631), 20 generations of random mating,
+    SBX (eta 20, p 1), polynomial mutation (eta 20, p 1/D), evaluation and
+    selection of 2N = 400,000 merged points, all in emo_nsga3_generation on
+    the device. Per generation: device time of the whole generation and of
+    its selection stages (CUDA events, L2 flushed before each); IGD of the
+    population to the H = 631 sphere front before and after."""
+    from paper_2503_20286_gb300 import workloads as wl
+    seed = wl.BASE_SEED + 4
+    R = torch.from_numpy(wl.das_dennis(H, M)).to(dev)
+    front = torch.from_numpy(wl.reference_front(H, M, "sphere")).to(dev)
+    X = torch.from_numpy(wl.decision_vectors(n, d, seed, stream=5)).to(dev)
+    F = emo.emo_standin_objectives(X, M, emo.EMO_SHAPE_SPHERE)
+    info = torch.zeros(8, dtype=torch.int32, device=dev)
+    ws = torch.empty(emo.emo_generation_workspace_size(n, d, M, R.shape[0]), dtype=torch.uint8, device=dev)
+    igd_ws = torch.empty(emo.emo_workspace_size(emo.EMO_OP_IGD, front.shape[0], M, 0), dtype=torch.uint8, device=dev)
+
+    def igd():
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        v = emo.emo_igd(F, front, ws=igd_ws, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return float(v.item()), a.elapsed_time(b)
+
+    igd0, igd_ms = igd()
+    emo.emo_set_stage_timing(True)
+    gen_ms, sel_ms = [], []
+    for g in range(gens):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        emo.emo_nsga3_generation(X, F, R, emo.EMO_SHAPE_SPHERE, seed, g, info=info, ws=ws, stream=stream)
+        b.record(stream)
+        sel_ms.append(sum(ms for _, ms in emo.emo_stage_times()))
+        torch.cuda.synchronize()
+        gen_ms.append(a.elapsed_time(b))
+    emo.emo_set_stage_timing(False)
+    if int(info[0].item()) != 0:
+        raise RuntimeError(f"generation status {int(info[0].item())} on the device")
+    igd1, _ = igd()
+    return {"loop": "NSGA-III, 20 generations on the device (emo_nsga3_generation)", "n": n, "n2": 2 * n, "m": M,
+            "d": d, "n_r": int(R.shape[0]), "sbx": {"eta": 20, "p": 1.0}, "pm": {"eta": 20, "p": 1.0 / d},
+            "generations": gens, "generation_ms": gen_ms, "selection_ms": sel_ms,
+            "generation_ms_mean": statistics.mean(gen_ms), "selection_ms_mean": statistics.mean(sel_ms),
+            "generations_per_s": 1e3 / statistics.mean(gen_ms),
+            "igd_initial": igd0, "igd_final": igd1, "igd_ms": igd_ms,
+            "igd_front": f"Das-Dennis H={H} directions projected onto the unit sphere",
+            "last_info": dict(zip(("status", "last_rank", "n_before", "n_last", "fallback_used", "n_recheck",
+                                   "n_fronts", "n_levels"), info.cpu().tolist()))}
+
+
+def _gpu_select_debug(emo, torch, dev, F, R, n_keep, seed, gen):
+    """One selection through the C ABI with every intermediate returned."""
+    n2, m = F.shape
+    Ft, Rt = torch.from_numpy(F).to(dev), torch.from_numpy(R).to(dev)
+    info = torch.zeros(8, dtype=torch.int32, device=dev)
+    dbg = {"rank": torch.empty(n2, dtype=torch.int32, device=dev), "z": torch.empty(m, device=dev),
+           "extreme": torch.empty(m, dtype=torch.int32, device=dev),
+           "a": torch.empty(m, dtype=torch.float64, device=dev), "fnorm": torch.empty(n2 * m, device=dev),
+           "pi": torch.empty(n2, dtype=torch.int32, device=dev),
+           "dist": torch.empty(n2, dtype=torch.float64, device=dev)}
+    surv = emo.emo_nsga3_select(Ft, Rt, n_keep, seed, gen, info=info, debug=dbg)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in dbg.items()}
+    out["fnorm"] = out["fnorm"].reshape(n2, m)
+    out["survivors"] = surv.cpu().numpy()
+    out["info"] = dict(zip(("status", "last_rank", "n_before", "n_last", "fallback_used", "n_recheck", "n_fronts",
+                            "n_levels"), info.cpu().tolist()))
+    return out, Ft, Rt
+
+
+def _gpu_select_ms(emo, torch, Ft, Rt, n_keep, seed, flush, stream, steps):
+    surv = torch.empty(n_keep, dtype=torch.int32, device=Ft.device)
+    nbytes = emo.emo_workspace_size(emo.EMO_OP_NSGA3_SELECT, Ft.shape[0], Ft.shape[1], Rt.shape[0])
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=Ft.device)
+    for g in range(2):
+        emo.emo_nsga3_select(Ft, Rt, n_keep, seed, g, survivors=surv, ws=ws)
+    ms = []
+    for k in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        emo.emo_nsga3_select(Ft, Rt, n_keep, seed, 2 + k, survivors=surv, ws=ws)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
+def _errors(g, S, fn64, z, a, pi, dist, rank, surv):
+    """Per-output comparison of the GPU intermediates with FP64 values over S."""
+    rel = np.abs(g["fnorm"][S].astype(np.float64) - fn64) / np.maximum(np.abs(fn64), 1e-300)
+    rel[fn64 == 0] = np.abs(g["fnorm"][S][fn64 == 0])
+    return {"survivors_equal": bool(np.array_equal(g["survivors"], surv)),
+            "ranks_equal_on_S": bool(rank is None or np.array_equal(g["rank"][S], rank)),
+            "z_equal": bool(np.array_equal(g["z"].astype(np.float64), z)),
+            "intercepts_fp64_equal": bool(np.array_equal(g["a"], a)),
+            "fnorm_fp32_max_rel_err": float(rel.max()) if rel.size else 0.0,
+            "pi_mismatches": None if pi is None else int(np.sum(g["pi"][S] != pi)),
+            "dist_fp64_max_abs_diff": None if dist is None else float(np.max(np.abs(g["dist"][S] - dist)))}
+
+
+def cpu_baseline_leg(emo, torch, dev, flush, stream, steps, F4, R4, n_keep4, seed4, main_ms):
+    """The oracle beside the GPU path: the FP64 CPU oracle timed on the host
+    cores (1 thread on workloads 0 and 1, all cores on workloads 0-2; the
+    2N = 400,000 workload from its committed fixture, written by the all-core
+    oracle), and the GPU's outputs compared with it per output: survivors,
+    ranks, z, FP64 intercepts, pi and FP64 distances exactly, normalised
+    objectives as the largest float32 relative error, the oracle's near-tie
+    count (two nearest lines within 1e-6 relative) and the GPU's FP64
+    re-checks. GPU selections/s per workload (median of `steps`, CUDA events,
+    L2 flushed before each)."""
+    import hashlib
+    import oracle
+    from paper_2503_20286_gb300 import workloads as wl
+    oracle.build()
+    par = oracle.has_parallel()
+    cores = oracle.threads(os.cpu_count() or 1) if par else 1
+    report = {}
+    for c in (0, 1, 2):
+        p = wl.config(c)
+        g, Ft, Rt = _gpu_select_debug(emo, torch, dev, p.F, p.R, p.n_keep, p.seed, p.generation)
+        ms = _gpu_select_ms(emo, torch, Ft, Rt, p.n_keep, p.seed, flush, stream, steps)
+        entry = {"workload": p.name, "gpu_ms": ms, "gpu_selections_per_s": 1e3 / ms,
+                 "gpu_n_recheck": g["info"]["n_recheck"]}
+        if c in (0, 1):
+            t0 = time.perf_counter()
+            oracle.nsga3_select(p.F, p.R, p.n_keep, p.seed, p.generation, trace=False)
+            entry["oracle_1_thread_s"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        surv, t = oracle.nsga3_select(p.F, p.R, p.n_keep, p.seed, p.generation, parallel=par)
+        entry[f"oracle_{cores}_threads_s"] = time.perf_counter() - t0
+        S = np.flatnonzero(t["rank"] <= t["last_rank"])
+        entry.update(_errors(g, S, t["fnorm"][S], t["z"], t["a"], t["pi"][S], t["dist"][S], t["rank"][S], surv))
+        entry["oracle_near_ties"] = t["near_ties"]
+        report[f"workload_{c}"] = entry
+    path = os.path.join(ROOT, "tests", "golden", "config4_oracle.npz")
+    if os.path.exists(path):
+        gold = np.load(path)
+        g, _, _ = _gpu_select_debug(emo, torch, dev, F4, R4, n_keep4, seed4, 0)
+        mask = np.unpackbits(gold["survivor_mask"], count=F4.shape[0], bitorder="little").astype(bool)
+        S = np.flatnonzero(gold["rank_u8"] != 255)
+        fn64 = (F4[S].astype(np.float64) - gold["z"]) / gold["a"]
+        entry = {"workload": "2N=400000 M=3 sphere H=631 (the timed population)", "gpu_ms": main_ms,
+                 "gpu_selections_per_s": 1e3 / main_ms, "gpu_n_recheck": g["info"]["n_recheck"],
+                 "oracle_fixture": "tests/golden/config4_oracle.npz",
+                 f"oracle_{int(gold['oracle_threads'])}_threads_s_when_written": float(gold["oracle_seconds"])}
+        entry.update(_errors(g, S, fn64, gold["z"], gold["a"], None, None,
+                             gold["rank_u8"][S].astype(np.int32), np.flatnonzero(mask)))
+        sha = lambda a: hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()  # noqa: E731
+        entry["pi_equal_sha256"] = sha(g["pi"][S].astype("<i4")) == str(gold["pi_sha256"])
+        entry["dist_fp64_equal_sha256"] = sha(g["dist"][S].astype("<f8")) == str(gold["dist_sha256"])
+        entry["oracle_near_ties"] = int(gold["near_ties"])
+        report["workload_4"] = entry
+    return report, cores
 
 
 def oracle_time(F, R, n_keep, seed, sample_n2: int):
@@ -552,6 +715,10 @@ def main():
             line["moead"] = moead_timing(emo, torch, dev, flush, stream, max(3, args.steps // 2))
         except Exception as e:  # reported in the line; the selection numbers above stand
             line["moead"] = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            line["generation_loop"] = generation_loop(emo, torch, dev, flush, stream)
+        except Exception as e:  # reported in the line; the selection numbers above stand
+            line["generation_loop"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and not args.no_batch:
         line["batched_vs_plain"] = batched_vs_plain(emo, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -559,6 +726,11 @@ def main():
         line["cpu_baseline"] = {"value": SAMPLE_N2 ** 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"first {SAMPLE_N2} points of the workload, {nr_s} Das-Dennis "
                                           f"directions, keep {SAMPLE_N2 // 2}; {dt:.1f} s"}
+        if not args.no_parity:
+            rep, cores = cpu_baseline_leg(emo, torch, dev, flush, stream, max(3, args.steps), F, R, n_keep, seed,
+                                          ms_per_step)
+            line["cpu_baseline"]["host_cores"] = cores
+            line["parity"] = rep
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
