@@ -19,6 +19,10 @@
  *    status word read by emo_workspace_status().
  *  - Several calls may run concurrently on different streams as long as each
  *    has its own workspace and outputs.
+ *  - The library sets up each device once per process (launch attributes,
+ *    occupancy, the address of the built-in scratch of
+ *    emo_nsga3_select_noalloc). After cudaDeviceReset on a device, do not
+ *    call the library on that device again in the same process.
  */
 #ifndef EMO_H
 #define EMO_H
@@ -330,8 +334,10 @@ emo_status emo_nsga3_generation(float* X, float* F, int64_t n, int64_t d, int32_
  * counterpart; this is a deployment convenience. The selection runs in an
  * 8 MiB scratch array built into the library (held on every GPU that loads
  * it until the process exits); populations with n2 <= 7168 and n_r <= 7168
- * (any m <= 16), or n2 <= 8192 and n_r <= 8192 (m <= 8), always fit on
- * devices with up to 304 SMs; what does not fit returns EMO_ERR_WORKSPACE. The call
+ * (any m <= 16) always fit on devices with up to 304 SMs, and n2 <= 8192
+ * with n_r <= 8192 (m <= 8) on devices with up to 152 SMs (the workspace
+ * grows with the CTAs of a cooperative launch, up to 2 per SM); what does
+ * not fit returns EMO_ERR_WORKSPACE. The call
  * makes no device allocation. Its first call on a device looks up the
  * scratch address (cudaGetSymbolAddress) and should come before any stream
  * capture. Calls share the scratch: every call initialises what it reads,

@@ -78,17 +78,22 @@ int main()
         }
     }
     // the allocation-free entry point's 8 MiB scratch holds the plan and one
-    // selection of 2N = n_r = 7168 at any m, 8192 at m <= 8 (up to 304 SMs)
+    // selection of 2N = n_r = 7168 at any m for cooperative launches of up
+    // to 608 CTAs (304 SMs at the largest occupancy used, 2), and of
+    // 2N = n_r = 8192 at m <= 8 for launches of up to 304 CTAs (152 SMs)
     const long long plan_bytes = (long long)((sizeof(Plan) + 255) / 256 * 256);
     for (int m = 2; m <= kMaxM; ++m) {
-        const long long n = m <= 8 ? 8192 : 7168;
-        ProbIn in{};
-        in.n2 = n;
-        in.m = m;
-        in.n_r = (int32_t)n;
-        in.mode = MODE_SELECT;
-        const long long need = plan_bytes + layout_problem(in, 304, nullptr, nullptr);
-        if (need > (8ll << 20)) return fail("no-alloc scratch", m, need);
+        for (int big = 0; big < 2; ++big) {
+            if (big && m > 8) continue;
+            const long long n = big ? 8192 : 7168;
+            ProbIn in{};
+            in.n2 = n;
+            in.m = m;
+            in.n_r = (int32_t)n;
+            in.mode = MODE_SELECT;
+            const long long need = plan_bytes + layout_problem(in, big ? 304 : 608, nullptr, nullptr);
+            if (need > (8ll << 20)) return fail("no-alloc scratch", m, need);
+        }
     }
     std::printf("layout ok\n");
     return 0;
