@@ -331,7 +331,7 @@ size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r)
 {
     if (!sizes_ok(n2, m)) return 0;
     if (op == EMO_OP_DOMINANCE) return 0;
-    if (op == EMO_OP_MOEAD_SELECT) return n_r >= 1 && n_r <= n2 ? (size_t)moead_layout(n2, n_r, nullptr, nullptr) : 0;
+    if (op == EMO_OP_MOEAD_SELECT) return n_r >= 1 && n_r <= n2 ? (size_t)moead_layout(n2, m, n_r, nullptr, nullptr) : 0;
     if (op == EMO_OP_IGD) return (size_t)(n2 * 8);
     int mode = op == EMO_OP_ND_RANK ? MODE_RANK
                : op == EMO_OP_NSGA3_SELECT ? MODE_SELECT
@@ -401,7 +401,7 @@ emo_status emo_moead_select(const float* X, const float* F1, const float* O, con
     if (!aligned(ws, 256)) return EMO_ERR_INVALID_ARG;
     MoeadArgs a;
     std::memset(&a, 0, sizeof(a));
-    if ((int64_t)ws_bytes < moead_layout(n, T, (char*)ws, &a)) return EMO_ERR_WORKSPACE;
+    if ((int64_t)ws_bytes < moead_layout(n, m, T, (char*)ws, &a)) return EMO_ERR_WORKSPACE;
     DevInfo di = dev_info();
     if (!di.ok) return EMO_ERR_CUDA;
     a.X = X;

@@ -38,10 +38,11 @@ struct MoeadArgs {
     unsigned long long* gmin;
     int32_t* tie;
     double* gpair;
+    double* sub;  // [n][m + 2]: ||w_j||, the subproblem's own PBI value, w_j / ||w_j||
 };
 // Workspace bytes of one TensorMOEA/D selection (regions 256-byte aligned);
 // fills the region pointers of `a` when `ws` is given.
-int64_t moead_layout(int64_t n, int32_t T, char* ws, MoeadArgs* a);
+int64_t moead_layout(int64_t n, int32_t m, int32_t T, char* ws, MoeadArgs* a);
 cudaError_t launch_moead_select(const MoeadArgs& a, int sms, cudaStream_t s);
 
 // One generation's offspring (random mating, SBX, PM; Appendix S.I).

@@ -16,7 +16,11 @@
 //     marked), so offspring 0 wins exactly when it is the lowest marked one.
 // Each PBI value is computed in FP64 from the float32 inputs with k
 // ascending and explicitly rounded operations (no contraction), so every
-// decision equals that of the same arithmetic done on a CPU.
+// decision equals that of the same arithmetic done on a CPU. What depends
+// only on the subproblem -- ||w||, the unit weights w / ||w|| and the
+// subproblem's own value g_old -- is computed once per subproblem (same
+// operations, so the same bits) and read by every pair of that subproblem;
+// a pair then needs one division and one square root.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -65,6 +69,23 @@ __device__ double pbi(const float* __restrict__ f, const float* __restrict__ w, 
     return __dadd_rn(d1, __dmul_rn(theta, __dsqrt_rn(dd)));
 }
 
+// pbi() of an offspring with the subproblem's ||w|| and unit weights taken
+// from `sub` (computed by the same operations in k_moead_prep).
+__device__ double pbi_pre(const float* __restrict__ f, const float* __restrict__ w, const double* __restrict__ sub,
+                          const float* z, int m, double theta)
+{
+    const double nw = __ldg(sub);
+    double fw = 0.0, dd = 0.0;
+    for (int k = 0; k < m; ++k)
+        fw = __dadd_rn(fw, __dmul_rn(__dsub_rn((double)__ldg(f + k), (double)z[k]), (double)__ldg(w + k)));
+    const double d1 = __ddiv_rn(fabs(fw), nw);
+    for (int k = 0; k < m; ++k) {
+        const double r = __dsub_rn(__dsub_rn((double)__ldg(f + k), (double)z[k]), __dmul_rn(d1, __ldg(sub + 2 + k)));
+        dd = __dadd_rn(dd, __dmul_rn(r, r));
+    }
+    return __dadd_rn(d1, __dmul_rn(theta, __dsqrt_rn(dd)));
+}
+
 __device__ __forceinline__ void load_zmin(const uint32_t* zkey, int m, float* z)
 {
     for (int k = 0; k < m; ++k) z[k] = fkey_inv(zkey[k]);
@@ -107,6 +128,28 @@ __global__ void __launch_bounds__(kMoeadThreads) k_moead_zmin(MoeadArgs a)
     }
 }
 
+// Per subproblem j: sub[j] = (||w_j||, g_old_j = PBI(F1_j | w_j, z_min),
+// w_j0 / ||w_j||, ..., w_j,m-1 / ||w_j||), in the operation order of pbi().
+__global__ void __launch_bounds__(kMoeadThreads) k_moead_prep(MoeadArgs a)
+{
+    float z[kMaxM];
+    load_zmin(a.zkey, a.m, z);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += stride) {
+        const float* w = a.W + j * a.m;
+        double* sub = a.sub + j * (a.m + 2);
+        double ww = 0.0;
+        for (int k = 0; k < a.m; ++k) {
+            const double wk = (double)__ldg(w + k);
+            ww = __dadd_rn(ww, __dmul_rn(wk, wk));
+        }
+        const double nw = __dsqrt_rn(ww);
+        sub[0] = nw;
+        for (int k = 0; k < a.m; ++k) sub[2 + k] = __ddiv_rn((double)__ldg(w + k), nw);
+        sub[1] = pbi(a.F1 + j * a.m, w, z, a.m, a.theta);
+    }
+}
+
 // One thread per (offspring i, neighbour slot t): mark and lower gmin[j].
 __global__ void __launch_bounds__(kMoeadThreads) k_moead_compare(MoeadArgs a)
 {
@@ -126,8 +169,9 @@ __global__ void __launch_bounds__(kMoeadThreads) k_moead_compare(MoeadArgs a)
         }
         for (int32_t u = 0; u < t && !dup; ++u) dup = __ldg(a.I_nb + i * a.T + u) == j;  // count a neighbour once
         if (!dup) {
-            const double g_old = pbi(a.F1 + (int64_t)j * a.m, a.W + (int64_t)j * a.m, z, a.m, a.theta);
-            const double g_new = pbi(a.F2 + i * a.m, a.W + (int64_t)j * a.m, z, a.m, a.theta);
+            const double* sub = a.sub + (int64_t)j * (a.m + 2);
+            const double g_old = __ldg(sub + 1);
+            const double g_new = pbi_pre(a.F2 + i * a.m, a.W + (int64_t)j * a.m, sub, z, a.m, a.theta);
             if (__dsub_rn(g_old, g_new) >= 0.0) {
                 g = g_new;
                 atomicMin(a.gmin + j, (unsigned long long)__double_as_longlong(g_new));
@@ -172,7 +216,7 @@ __global__ void __launch_bounds__(kMoeadThreads) k_moead_gather(MoeadArgs a)
             if (bad || !(ww > 0.0)) set_status(a.status, EMO_ERR_NONFINITE);
             const unsigned long long gm = a.gmin[j];
             if (gm != kNoMark) {
-                const double g_old = pbi(f1, w, z, a.m, a.theta);
+                const double g_old = a.sub[j * (a.m + 2) + 1];
                 const double best = __longlong_as_double((long long)gm);
                 const int32_t tie = a.tie[j];
                 win = best < g_old ? tie : (tie == 0 ? 0 : -1);
@@ -200,19 +244,21 @@ __global__ void k_moead_finish(MoeadArgs a)
 
 }  // namespace
 
-int64_t moead_layout(int64_t n, int32_t T, char* ws, MoeadArgs* a)
+int64_t moead_layout(int64_t n, int32_t m, int32_t T, char* ws, MoeadArgs* a)
 {
     auto up = [](int64_t b) { return (b + 255) / 256 * 256; };
     const int64_t off_gmin = 256;                       // status word at 0, z_min keys at 64
     const int64_t off_tie = up(off_gmin + 8 * n);
     const int64_t off_pair = up(off_tie + 4 * n);
-    const int64_t total = up(off_pair + 8 * n * (int64_t)T);
+    const int64_t off_sub = up(off_pair + 8 * n * (int64_t)T);
+    const int64_t total = up(off_sub + 8 * n * (int64_t)(m + 2));
     if (ws && a) {
         a->status = (int32_t*)ws;
         a->zkey = (uint32_t*)(ws + 64);
         a->gmin = (unsigned long long*)(ws + off_gmin);
         a->tie = (int32_t*)(ws + off_tie);
         a->gpair = (double*)(ws + off_pair);
+        a->sub = (double*)(ws + off_sub);
     }
     return total;
 }
@@ -226,6 +272,7 @@ cudaError_t launch_moead_select(const MoeadArgs& a, int sms, cudaStream_t s)
     const int64_t pairs = a.n * (int64_t)a.T;
     k_moead_init<<<grid_for(a.n, kMoeadThreads, 8), kMoeadThreads, 0, s>>>(a);
     k_moead_zmin<<<grid_for(a.n, kMoeadThreads, 4), kMoeadThreads, 0, s>>>(a);
+    k_moead_prep<<<grid_for(a.n, kMoeadThreads, 8), kMoeadThreads, 0, s>>>(a);
     k_moead_compare<<<grid_for(pairs, kMoeadThreads, 16), kMoeadThreads, 0, s>>>(a);
     k_moead_tie<<<grid_for(pairs, kMoeadThreads, 16), kMoeadThreads, 0, s>>>(a);
     k_moead_gather<<<grid_for(a.n, kMoeadThreads / 32, 16), kMoeadThreads, 0, s>>>(a);
