@@ -360,19 +360,40 @@ emo_status emo_get_last_device_status(emo_stream_t stream, int32_t* status_out);
 
 /* Offline tuning of the launch shapes for populations of m objectives and
  * about n2 points (same floor(log2 n2)) on the current device's
- * architecture: the
- * association kernel's blocks per SM, timed on a synthetic population (a
- * sphere-shaped front and n2/2 directions on the simplex) over the
- * candidates 2, 4, 8, 16, 32. It allocates device memory and synchronises,
- * so it belongs outside timed regions and graph captures. With a non-null
- * `cache_path`, results found in that text file (lines "arch m bucket
- * blocks", arch = 10 * major + minor compute capability, bucket =
- * floor(log2 n2)) are loaded and reused, and a new result is appended. Later
- * calls of the same process use the tuned shape, and the first selection of
- * a process loads the file named by the environment variable
- * EMO_AUTOTUNE_CACHE, if set; survivors do not depend on the shape.
+ * architecture, by a coordinate search timed with the stage events on a
+ * synthetic population (a sphere-shaped front and n2/2 directions on the
+ * simplex), each candidate the best of three selections, in this order:
+ *   1. dominance work-item size (row blocks per item: 64 .. 1024) by the
+ *      dominance kernel's time;
+ *   2. the per-front schedule of the peeling: how many CTAs serve a front
+ *      (every CTA, half, a quarter, ... down to a single CTA, whose fronts
+ *      then need no grid barrier) by the peeling time;
+ *   3. the CTAs of the other cooperative stages (sort, statistics, CSR,
+ *      niching, survivors; at most as many as step 2) by their summed time;
+ *   4. the association kernel's blocks per SM (2, 4, 8, 16, 32).
+ * It allocates device memory and synchronises, so it belongs outside timed
+ * regions and graph captures. With a non-null `cache_path`, results found in
+ * that text file (lines "arch m bucket assoc_bps dom_chunk cap_wide
+ * cap_narrow", arch = 10 * major + minor compute capability, bucket =
+ * floor(log2 n2), a cap of 0 = every CTA) are loaded and reused, and a new
+ * result is appended. Later calls of the same process use the tuned shapes,
+ * and the first selection of a process loads the file named by the
+ * environment variable EMO_AUTOTUNE_CACHE, if set. Untuned sizes use 8
+ * association blocks per SM, the largest dominance items that give every SM
+ * at least two, and no caps. Survivors do not depend on the shapes.
  * EMO_ERR_INVALID_ARG for n2 < 64 or sizes out of range. */
 emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path);
+
+/* The launch shapes a selection of n2 points with m objectives would use on
+ * the current device now (tuned or default): shape_out[0] association
+ * blocks per SM, [1] dominance row blocks per work item, [2] CTAs of the
+ * peeling group, [3] CTAs of the other cooperative groups (a batch can give
+ * a population fewer). */
+emo_status emo_launch_shape(int32_t m, int64_t n2, int32_t* shape_out);
+
+/* Forgets every tuned shape of this process (later calls use the defaults
+ * until emo_autotune runs or EMO_AUTOTUNE_CACHE is loaded again). */
+void emo_autotune_reset(void);
 
 /* Bounded-wait budget (in SM clock cycles) for the device-side barriers of
  * later calls in this process; 0 restores the default (about 2 s). */

@@ -100,6 +100,10 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
                                                i32, vp, vp, sz, vp]
             L.emo_autotune.restype = ctypes.c_int
             L.emo_autotune.argtypes = [i32, i64, ctypes.c_char_p]
+            L.emo_launch_shape.restype = ctypes.c_int
+            L.emo_launch_shape.argtypes = [i32, i64, ctypes.c_void_p]
+            L.emo_autotune_reset.restype = None
+            L.emo_autotune_reset.argtypes = []
             L.emo_get_last_device_status.restype = ctypes.c_int
             L.emo_get_last_device_status.argtypes = [vp, vp]
             L.emo_hype_select.restype = ctypes.c_int
@@ -379,6 +383,19 @@ def emo_workspace_status(ws: torch.Tensor, stream=None) -> int:
     out = ctypes.c_int32(0)
     _check(lib().emo_workspace_status(_ptr(ws), _stream(stream), ctypes.byref(out)), "emo_workspace_status")
     return int(out.value)
+
+
+def emo_launch_shape(m: int, n2: int) -> dict:
+    """Launch shapes a selection of (n2, m) uses now on the current device."""
+    out = (ctypes.c_int32 * 4)()
+    _check(lib().emo_launch_shape(int(m), int(n2), ctypes.addressof(out)), "emo_launch_shape")
+    return {"assoc_blocks_per_sm": out[0], "dom_rowblocks_per_item": out[1], "peel_ctas": out[2],
+            "other_coop_ctas": out[3]}
+
+
+def emo_autotune_reset() -> None:
+    """Forget the tuned shapes of this process."""
+    lib().emo_autotune_reset()
 
 
 def emo_autotune(m: int, n2: int, cache_path: str | None = None) -> None:

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <string>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -149,14 +150,18 @@ cudaError_t coop(const void* fn, int G, size_t smem, cudaStream_t s, Plan* plan)
     return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCoopThreads), args, smem, s);
 }
 
-// Launch the whole pipeline for problems already laid out in `ins` (ordered
-// by objective count).
-// Launch shapes chosen by emo_autotune, per (compute capability as
-// 10 * major + minor, m, floor(log2 n2)): the association kernel's blocks
-// per SM. Absent = the default (8).
+// Launch shapes, per (compute capability as 10 * major + minor, m,
+// floor(log2 n2)); survivors never depend on them. emo_autotune measures
+// them; untuned sizes take default_shape().
+struct Shape {
+    int assoc_bps;   // association kernel: blocks per SM
+    int dom_chunk;   // dominance: row blocks per work item (64 .. 1024, a power of two)
+    int cap_wide;    // CTAs of the peeling / TensorHypE group of one problem (0 = no cap)
+    int cap_narrow;  // CTAs of the other cooperative groups (0 = no cap)
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tune;
-std::atomic<int> g_force_assoc_bps{0};  // set only while emo_autotune times a candidate
+std::map<std::tuple<int, int, int>, Shape> g_tune;
+Shape g_force{0, 0, -1, -1};  // set only while emo_autotune times a candidate (0 / -1 = not forced)
 
 int size_bucket(int64_t n2)
 {
@@ -173,29 +178,51 @@ int device_arch(int dev)
     return ma * 10 + mi;
 }
 
-// Cache file: one "arch m bucket blocks_per_sm" line per tuned shape.
+// Cache file: one line per tuned size, "arch m bucket assoc_bps" optionally
+// followed by "dom_chunk cap_wide cap_narrow".
 void load_tune_cache(const char* path)
 {
     FILE* fh = path ? std::fopen(path, "r") : nullptr;
     if (!fh) return;
-    int ca = 0, cm = 0, cb = 0, cv = 0;
+    char line[256];
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    while (std::fscanf(fh, "%d %d %d %d", &ca, &cm, &cb, &cv) == 4)
-        if (cv >= 1 && cv <= 64) g_tune[std::make_tuple(ca, cm, cb)] = cv;
+    while (std::fgets(line, sizeof(line), fh)) {
+        int v[7] = {0, 0, 0, 0, kDomRowChunk, 0, 0};
+        const int n = std::sscanf(line, "%d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6]);
+        if ((n != 4 && n != 7) || v[3] < 1 || v[3] > 64 || !dom_chunk_ok(v[4]) || v[5] < 0 || v[6] < 0) continue;
+        g_tune[std::make_tuple(v[0], v[1], v[2])] = Shape{v[3], v[4], v[5], v[6]};
+    }
     std::fclose(fh);
 }
 
-int assoc_blocks_per_sm(int dev, int m, int64_t n2)
+// Without tuning: 8 association blocks per SM, the largest dominance items
+// that still give every SM two or more, no group caps.
+Shape default_shape(int sms, int64_t n2)
 {
-    if (int f = g_force_assoc_bps.load()) return f;
-    static std::once_flag env_once;  // shapes tuned by earlier processes
-    std::call_once(env_once, [] { load_tune_cache(std::getenv("EMO_AUTOTUNE_CACHE")); });
-    const int arch = device_arch(dev);
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune.find(std::make_tuple(arch, m, size_bucket(n2)));
-    return it == g_tune.end() ? 8 : it->second;
+    Shape sh{8, kDomRowChunk, 0, 0};
+    while (sh.dom_chunk > kDomChunkMin && dom_items_of(n2, sh.dom_chunk) < 2ll * sms) sh.dom_chunk >>= 1;
+    return sh;
 }
 
+Shape shape_for(int dev, int sms, int m, int64_t n2)
+{
+    static std::once_flag env_once;  // shapes tuned by earlier processes
+    std::call_once(env_once, [] { load_tune_cache(std::getenv("EMO_AUTOTUNE_CACHE")); });
+    Shape sh = default_shape(sms, n2);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(std::make_tuple(device_arch(dev), m, size_bucket(n2)));
+        if (it != g_tune.end()) sh = it->second;
+        if (g_force.assoc_bps > 0) sh.assoc_bps = g_force.assoc_bps;
+        if (g_force.dom_chunk > 0) sh.dom_chunk = g_force.dom_chunk;
+        if (g_force.cap_wide >= 0) sh.cap_wide = g_force.cap_wide;
+        if (g_force.cap_narrow >= 0) sh.cap_narrow = g_force.cap_narrow;
+    }
+    return sh;
+}
+
+// Launch the whole pipeline for problems already laid out in `ins` (ordered
+// by objective count).
 emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t s)
 {
     DevInfo di = dev_info();
@@ -206,7 +233,13 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
     int64_t off = kPlanBytes;
     int max_ncb = 1;
     bool any_select = false, any_hype = false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EMO_ERR_CUDA;
     for (auto& in : ins) {
+        const Shape sh = shape_for(dev, di.sms, in.m, in.n2);
+        in.dom_chunk = sh.dom_chunk;
+        in.cap_wide = sh.cap_wide;
+        in.cap_narrow = sh.cap_narrow;
         in.ws_off = (uint64_t)off;
         off += layout_problem(in, di.G, nullptr, nullptr);
         max_ncb = std::max<int>(max_ncb, (int)cdiv(in.n2, kColBlock));
@@ -239,7 +272,10 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
     for (int p = 0; p < nprob;) {
         int q = p;
         long long hi = item;
-        while (q < nprob && ins[q].m == ins[p].m) hi += dom_items_of(ins[q++].n2);
+        while (q < nprob && ins[q].m == ins[p].m) {
+            hi += dom_items_of(ins[q].n2, ins[q].dom_chunk);
+            ++q;
+        }
         if (launch_dominance_tri_range(ins[p].m, plan, di.sms, s, item, hi, &plan->dom_ctr[ins[p].m], p, q) !=
             cudaSuccess)
             return EMO_ERR_CUDA;
@@ -255,11 +291,10 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
         sm.mark("stats");
         std::vector<int> m_of(nprob);
         for (int p = 0; p < nprob; ++p) m_of[p] = ins[p].m;
-        int dev = 0, big = 0;
-        cudaGetDevice(&dev);
+        int big = 0;
         for (int p = 1; p < nprob; ++p)
             if (ins[p].n2 > ins[big].n2) big = p;
-        const int bps = assoc_blocks_per_sm(dev, ins[big].m, ins[big].n2);
+        const int bps = shape_for(dev, di.sms, ins[big].m, ins[big].n2).assoc_bps;
         if (launch_assoc(plan, nprob, m_of.data(), di.sms, bps, s) != cudaSuccess) return EMO_ERR_CUDA;
         sm.mark("assoc");
         k_rescan<<<di.sms * 2, 256, 0, s>>>(plan);
@@ -629,10 +664,11 @@ emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path)
     }
     const size_t wsb = emo_workspace_size(EMO_OP_NSGA3_SELECT, n2, m, (int32_t)n_r);
     if (wsb == 0) return EMO_ERR_INVALID_ARG;
+    DevInfo di = dev_info();
+    if (!di.ok) return EMO_ERR_CUDA;
     void *dF = nullptr, *dR = nullptr, *dS = nullptr, *dW = nullptr;
     emo_status st = EMO_OK;
-    int best = 8;
-    float best_ms = INFINITY;
+    Shape best = default_shape(di.sms, n2);
     if (cudaMalloc(&dF, F.size() * 4) != cudaSuccess || cudaMalloc(&dR, R.size() * 4) != cudaSuccess ||
         cudaMalloc(&dS, (size_t)(n2 / 2 + 1) * 4) != cudaSuccess || cudaMalloc(&dW, wsb) != cudaSuccess ||
         cudaMemcpy(dF, F.data(), F.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -640,23 +676,72 @@ emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path)
         st = EMO_ERR_CUDA;
     } else {
         const int prev_timing = g_timing.exchange(1);
-        for (int cand : {2, 4, 8, 16, 32}) {  // the association stage, best of three calls
-            g_force_assoc_bps.store(cand);
-            float ms_best = INFINITY;
-            for (int rep = 0; rep < 3 && st == EMO_OK; ++rep) {
+        // Sum over three selections of the named stages' device times with
+        // shape `sh` forced (the first selection also warms up), or +inf.
+        auto timed = [&](const Shape& sh, std::initializer_list<const char*> stages) {
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_force = sh;
+            }
+            float best_ms = INFINITY;
+            for (int rep = 0; rep < 4 && st == EMO_OK; ++rep) {
                 st = emo_nsga3_select((const float*)dF, n2, m, (const float*)dR, (int32_t)n_r, n2 / 2, 1, rep,
                                       (int32_t*)dS, nullptr, dW, wsb, nullptr);
                 float ms[32];
                 const char* names[32];
                 const int ns = st == EMO_OK ? emo_stage_times(ms, names, 32) : -1;
-                if (ns < 0) st = st == EMO_OK ? EMO_ERR_CUDA : st;
+                if (ns < 0) {
+                    if (st == EMO_OK) st = EMO_ERR_CUDA;
+                    break;
+                }
+                float sum = 0.0f;
                 for (int i = 0; i < ns; ++i)
-                    if (std::strcmp(names[i], "assoc") == 0) ms_best = std::min(ms_best, ms[i]);
+                    for (const char* nm : stages)
+                        if (std::strcmp(names[i], nm) == 0) sum += ms[i];
+                if (rep > 0) best_ms = std::min(best_ms, sum);
             }
-            if (st != EMO_OK) break;
-            if (ms_best < best_ms) { best_ms = ms_best; best = cand; }
+            return best_ms;
+        };
+        // coordinate search, one shape parameter at a time in pipeline order
+        float bms = INFINITY;
+        for (int c = kDomChunkMin; c <= kDomRowChunk && st == EMO_OK; c <<= 1) {
+            Shape t = best;
+            t.dom_chunk = c;
+            const float v = timed(t, {"dominance"});
+            if (v < bms) { bms = v; best.dom_chunk = c; }
         }
-        g_force_assoc_bps.store(0);
+        std::vector<int> caps = {0};
+        for (int c = di.G / 2; c >= 1; c /= 2) caps.push_back(c);
+        bms = INFINITY;
+        for (int c : caps) {
+            if (st != EMO_OK) break;
+            Shape t = best;
+            t.cap_wide = c;
+            t.cap_narrow = 0;
+            const float v = timed(t, {"peel"});
+            if (v < bms) { bms = v; best.cap_wide = c; }
+        }
+        bms = INFINITY;
+        for (int c : caps) {
+            if (st != EMO_OK) break;
+            if (best.cap_wide > 0 && (c == 0 || c > best.cap_wide)) continue;
+            Shape t = best;
+            t.cap_narrow = c;
+            const float v = timed(t, {"sort", "stats", "csr", "niche", "finish"});
+            if (v < bms) { bms = v; best.cap_narrow = c; }
+        }
+        bms = INFINITY;
+        for (int c : {2, 4, 8, 16, 32}) {
+            if (st != EMO_OK) break;
+            Shape t = best;
+            t.assoc_bps = c;
+            const float v = timed(t, {"assoc"});
+            if (v < bms) { bms = v; best.assoc_bps = c; }
+        }
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_force = Shape{0, 0, -1, -1};
+        }
         g_timing.store(prev_timing);
     }
     cudaFree(dF); cudaFree(dR); cudaFree(dS); cudaFree(dW);
@@ -667,10 +752,32 @@ emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path)
     }
     if (cache_path)
         if (FILE* fh = std::fopen(cache_path, "a")) {
-            std::fprintf(fh, "%d %d %d %d\n", arch, (int)m, size_bucket(n2), best);
+            std::fprintf(fh, "%d %d %d %d %d %d %d\n", arch, (int)m, size_bucket(n2), best.assoc_bps, best.dom_chunk,
+                         best.cap_wide, best.cap_narrow);
             std::fclose(fh);
         }
     return EMO_OK;
+}
+
+emo_status emo_launch_shape(int32_t m, int64_t n2, int32_t* shape_out)
+{
+    if (!sizes_ok(n2, m) || !shape_out) return EMO_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EMO_ERR_CUDA;
+    DevInfo di = dev_info();
+    if (!di.ok) return EMO_ERR_CUDA;
+    const Shape sh = shape_for(dev, di.sms, m, n2);
+    shape_out[0] = sh.assoc_bps;
+    shape_out[1] = sh.dom_chunk;
+    shape_out[2] = sh.cap_wide > 0 ? std::min(sh.cap_wide, di.G) : di.G;
+    shape_out[3] = sh.cap_narrow > 0 ? std::min(sh.cap_narrow, shape_out[2]) : shape_out[2];
+    return EMO_OK;
+}
+
+void emo_autotune_reset(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
 }
 
 const char* emo_status_string(int status)

@@ -34,7 +34,8 @@ constexpr int kMaxBatch = EMO_MAX_BATCH;
 constexpr int kTileRows = 32;         // rows per row block
 constexpr int kTileWords = 32;        // words per tile row
 constexpr int kColBlock = 1024;       // columns per column block
-constexpr int kDomRowChunk = 1024;    // row blocks per dominance work item
+constexpr int kDomRowChunk = 1024;    // row blocks per dominance work item (largest; emo_dominance)
+constexpr int kDomChunkMin = 64;      // smallest row-block chunk of a selection's dominance items
 constexpr int kCoopThreads = 512;     // threads of the cooperative kernels
 constexpr int kNicheBins = 4096;      // niching select: bins of the top 12 bits of a priority
 constexpr int kRadixBits = 8;
@@ -64,6 +65,12 @@ struct ProbIn {
     int32_t* last_rank_out;  // nullable
     emo_select_debug dbg;
     uint64_t ws_off;         // byte offset of this problem's region
+    // launch shapes (tuned per device, objective count and size; survivors
+    // never depend on them)
+    int32_t dom_chunk;       // row blocks per dominance work item: 64 .. 1024, a power of two
+    int32_t cap_wide;        // most CTAs of the peeling (and TensorHypE) group; 0 = no cap
+    int32_t cap_narrow;      // most CTAs of the sort / statistics / CSR / niching / survivor groups; 0 = no cap
+    int32_t pad_shape_;
 };
 
 // Per-problem scalars; zeroed by the prep kernel.
@@ -140,7 +147,8 @@ struct Plan {
     int32_t nprob;
     int32_t G;               // CTAs of every cooperative launch
     long long spin_budget;   // cycles a bounded wait may spin
-    int32_t grp_first[kMaxBatch + 1];     // cooperative CTA groups
+    int32_t grp_first[kMaxBatch + 1];     // cooperative CTA groups of the peeling and TensorHypE kernels
+    int32_t grpn_first[kMaxBatch + 1];    // groups of the other cooperative kernels (at most as large)
     long long dom_item_start[kMaxBatch + 1];
     long long dom_items;
     unsigned long long dom_ctr[kMaxM + 1];  // dynamic work counters per objective count
@@ -300,26 +308,31 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
 }
 
 // Dominance work items of one problem: column block cb covers row blocks
-// [0, min(nrb, 32 (cb + 1))), split into chunks of kDomRowChunk row blocks.
-__host__ __device__ __forceinline__ int64_t dom_items_of_cb(int64_t cb, int64_t nrb)
+// [0, min(nrb, 32 (cb + 1))), split into chunks of `chunk` row blocks (a
+// power of two from kDomChunkMin to kDomRowChunk).
+__host__ __device__ __forceinline__ int64_t dom_items_of_cb(int64_t cb, int64_t nrb, int64_t chunk)
 {
     int64_t rbs = nrb < 32 * (cb + 1) ? nrb : 32 * (cb + 1);
-    return cdiv(rbs, kDomRowChunk);
+    return cdiv(rbs, chunk);
 }
-// Items of column blocks 0 .. c-1 in closed form: with B = kDomRowChunk / 32
+// Items of column blocks 0 .. c-1 in closed form: with B = chunk / 32
 // column blocks' worth of row blocks per item, block cb < nrb / 32 has
-// cb / B + 1 items (its 32 (cb + 1) row blocks in chunks of kDomRowChunk),
-// every later block has cdiv(nrb, kDomRowChunk).
-static_assert(kDomRowChunk % 32 == 0 && (kDomRowChunk / 32) % 2 == 0, "dom_items_prefix assumes an even B");
-__host__ __device__ __forceinline__ int64_t dom_items_prefix(int64_t c, int64_t nrb)
+// cb / B + 1 items (its 32 (cb + 1) row blocks in chunks of `chunk`),
+// every later block has cdiv(nrb, chunk).
+static_assert(kDomChunkMin % 64 == 0 && kDomRowChunk % 64 == 0, "dom_items_prefix assumes an even B");
+__host__ __device__ __forceinline__ int64_t dom_items_prefix(int64_t c, int64_t nrb, int64_t chunk)
 {
-    constexpr int64_t B = kDomRowChunk / 32;
+    const int64_t B = chunk / 32;
     const int64_t A = nrb / 32, a = c < A ? c : A, q = a / B, r = a % B;
-    return (q + 1) * (B / 2 * q + r) + (c > A ? (c - A) * cdiv(nrb, kDomRowChunk) : 0);
+    return (q + 1) * (B / 2 * q + r) + (c > A ? (c - A) * cdiv(nrb, chunk) : 0);
 }
-__host__ __device__ inline int64_t dom_items_of(int64_t n2)
+__host__ __device__ inline int64_t dom_items_of(int64_t n2, int64_t chunk)
 {
-    return dom_items_prefix(cdiv(n2, kColBlock), cdiv(n2, 32));
+    return dom_items_prefix(cdiv(n2, kColBlock), cdiv(n2, 32), chunk);
+}
+__host__ __device__ inline bool dom_chunk_ok(int64_t chunk)
+{
+    return chunk >= kDomChunkMin && chunk <= kDomRowChunk && (chunk & (chunk - 1)) == 0;
 }
 
 constexpr int kAscPointsPerItem = 2048;
@@ -376,14 +389,19 @@ struct Group {
     int rank;    // CTA rank inside the group
     int size;    // CTAs in the group
 };
-__device__ __forceinline__ Group group_of(const Plan* plan)
+// The group of this CTA in the wide (peeling, TensorHypE) or the narrow
+// (every other cooperative kernel) assignment; prob = -1 for a CTA that
+// serves no problem (groups are capped by the problems' launch shapes), which
+// returns at once.
+__device__ __forceinline__ Group group_of(const Plan* plan, bool wide)
 {
+    const int32_t* first = wide ? plan->grp_first : plan->grpn_first;
     Group g;
     int b = blockIdx.x, p = 0;
-    while (p + 1 < plan->nprob && plan->grp_first[p + 1] <= b) ++p;
-    g.prob = p;
-    g.rank = b - plan->grp_first[p];
-    g.size = plan->grp_first[p + 1] - plan->grp_first[p];
+    while (p + 1 < plan->nprob && first[p + 1] <= b) ++p;
+    g.prob = b < first[plan->nprob] ? p : -1;
+    g.rank = b - first[p];
+    g.size = first[p + 1] - first[p];
     return g;
 }
 

@@ -50,19 +50,20 @@ struct PrefShape {
 };
 
 // Decode a dominance item of one problem: column blocks are served from the
-// last (tallest) to the first; each is split into chunks of kDomRowChunk row
-// blocks. Binary search over the closed-form item prefix.
-__device__ __forceinline__ void dom_decode(long long local, int ncb, int nrb, int& cb, int& chunk)
+// last (tallest) to the first; each is split into chunks of `rows` row
+// blocks (the problem's dom_chunk). Binary search over the closed-form item
+// prefix.
+__device__ __forceinline__ void dom_decode(long long local, int ncb, int nrb, int rows, int& cb, int& chunk)
 {
-    const long long u = dom_items_prefix(ncb, nrb) - local;  // in 1 .. total
-    int lo = 1, hi = ncb;                                     // smallest c with prefix(c) >= u
+    const long long u = dom_items_prefix(ncb, nrb, rows) - local;  // in 1 .. total
+    int lo = 1, hi = ncb;                                           // smallest c with prefix(c) >= u
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (dom_items_prefix(mid, nrb) >= u) hi = mid;
+        if (dom_items_prefix(mid, nrb, rows) >= u) hi = mid;
         else lo = mid + 1;
     }
     cb = lo - 1;
-    chunk = (int)(dom_items_prefix(lo, nrb) - u);
+    chunk = (int)(dom_items_prefix(lo, nrb, rows) - u);
 }
 
 // Flush a warp's per-lane column counters into s_cnt (column q of the block
@@ -387,7 +388,8 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
         while (p + 1 < plan->nprob && plan->dom_item_start[p + 1] <= item) ++p;
         const ProbDev& d = plan->p[p];
         int cb, chunk;
-        dom_decode(item - plan->dom_item_start[p], d.ncb, d.nrb, cb, chunk);
+        const int rows = d.in.dom_chunk;
+        dom_decode(item - plan->dom_item_start[p], d.ncb, d.nrb, rows, cb, chunk);
         bool fatal = false;
         if (!dom_stage(d, cb, K, S::OBJ_BYTES, sm.obj, sm.rs, sm.cnt, &sm.bar, &sm.skip, parity, fatal)) {
             if (fatal) break;
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
         }
         const int64_t n2 = d.in.n2;
         const int rbmax = min(d.nrb, 32 * (cb + 1));
-        const int rb_lo = chunk * kDomRowChunk, rb_hi = min(rbmax, rb_lo + kDomRowChunk);
+        const int rb_lo = chunk * rows, rb_hi = min(rbmax, rb_lo + rows);
         const int dupcut = d.minrs[cb];
         const int64_t cbase = (int64_t)cb * kColBlock;
         // in registers: the tile stores could alias the plan, which would
@@ -468,7 +470,8 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
         while (p + 1 < plan->nprob && plan->dom_item_start[p + 1] <= item) ++p;
         const ProbDev& d = plan->p[p];
         int cb, chunk;
-        dom_decode(item - plan->dom_item_start[p], d.ncb, d.nrb, cb, chunk);
+        const int rows = d.in.dom_chunk;
+        dom_decode(item - plan->dom_item_start[p], d.ncb, d.nrb, rows, cb, chunk);
         bool fatal = false;
         if (!dom_stage(d, cb, K, G.obj_bytes, obj, rs, cnt, bar, s_skip, parity, fatal)) {
             if (fatal) break;
@@ -476,7 +479,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
         }
         const int64_t n2 = d.in.n2;
         const int rbmax = min(d.nrb, 32 * (cb + 1));
-        const int rb_lo = chunk * kDomRowChunk, rb_hi = min(rbmax, rb_lo + kDomRowChunk);
+        const int rb_lo = chunk * rows, rb_hi = min(rbmax, rb_lo + rows);
         const int dupcut = d.minrs[cb];
         const int64_t cbase = (int64_t)cb * kColBlock;
         uint32_t* const Dm = d.D;

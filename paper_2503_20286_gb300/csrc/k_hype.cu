@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_hype(Plan* plan)
     __shared__ float s_pts[kHypeTile];
     __shared__ RadixSmem rsm;
     __shared__ uint32_t s_key[kMaxM];
-    const Group g = group_of(plan);
+    const Group g = group_of(plan, true);
+    if (g.prob < 0) return;  // a CTA beyond every problem's group
     const ProbDev& d = plan->p[g.prob];
     const ProbIn& in = d.in;
     const long long budget = plan->spin_budget;

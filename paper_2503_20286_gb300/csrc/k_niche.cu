@@ -19,7 +19,8 @@ namespace emo {
 // ------------------------------------------------------------ k_csr
 __global__ void __launch_bounds__(kCoopThreads, 1) k_csr(Plan* plan)
 {
-    const Group g = group_of(plan);
+    const Group g = group_of(plan, false);
+    if (g.prob < 0) return;  // a CTA beyond every problem's group
     const ProbDev& d = plan->p[g.prob];
     const ProbIn& in = d.in;
     const long long budget = plan->spin_budget;
@@ -244,7 +245,8 @@ __device__ __forceinline__ unsigned long long niche_key(uint64_t seed, uint64_t 
 __global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
 {
     __shared__ NicheSmem sm;
-    const Group g = group_of(plan);
+    const Group g = group_of(plan, false);
+    if (g.prob < 0) return;  // a CTA beyond every problem's group
     const ProbDev& d = plan->p[g.prob];
     const ProbIn& in = d.in;
     const long long budget = plan->spin_budget;
@@ -359,7 +361,8 @@ __device__ __forceinline__ unsigned long long oneshot_key(uint64_t seed, uint64_
 __global__ void __launch_bounds__(kCoopThreads, 1) k_niche_oneshot(Plan* plan)
 {
     __shared__ NicheSmem sm;
-    const Group g = group_of(plan);
+    const Group g = group_of(plan, false);
+    if (g.prob < 0) return;  // a CTA beyond every problem's group
     const ProbDev& d = plan->p[g.prob];
     const ProbIn& in = d.in;
     const long long budget = plan->spin_budget;
@@ -441,7 +444,8 @@ cudaError_t sticky_merge(const int32_t* status, cudaStream_t s)
 // and the optional intermediates.
 __global__ void __launch_bounds__(kCoopThreads, 1) k_finish(Plan* plan)
 {
-    const Group g = group_of(plan);
+    const Group g = group_of(plan, false);
+    if (g.prob < 0) return;  // a CTA beyond every problem's group
     const ProbDev& d = plan->p[g.prob];
     const ProbIn& in = d.in;
     Scal* sc = d.sc;

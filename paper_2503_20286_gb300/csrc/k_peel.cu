@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
     // [ring] per-warp copy stages | [ncb + 1] member prefix per block | [kPeelChunk] staged members
     extern __shared__ __align__(128) int s_dyn[];
 
-    const Group g = group_of(plan);
+    const Group g = group_of(plan, true);
+    if (g.prob < 0) return;  // a CTA beyond every problem's group
     const ProbDev& d = plan->p[g.prob];
     const ProbIn& in = d.in;
     const long long budget = plan->spin_budget;

@@ -33,25 +33,39 @@ __global__ void k_setup(SetupArgs a, Plan* plan, char* ws)
         for (int i = 0; i <= kMaxM; ++i) plan->dom_ctr[i] = 0;
         plan->asc_next = 0;
         plan->status = 0;
-        // CTA groups proportional to n2^2 (the dominance and peeling work),
-        // at least one CTA each.
+        // Wide CTA groups (peeling, TensorHypE) proportional to n2^2 (the
+        // dominance and peeling work), at least one CTA each and at most the
+        // problem's cap_wide; narrow groups (the other cooperative kernels)
+        // the first min(wide, cap_narrow) CTAs' worth. CTAs beyond the
+        // groups serve no problem.
         double tot = 0.0;
         for (int p = 0; p < a.nprob; ++p) tot += (double)a.in[p].n2 * (double)a.in[p].n2;
         int extra = a.G - a.nprob, given = 0;
         int cnt[kMaxBatch];
+        auto cap_of = [&](int p, int32_t c) { return c > 0 ? c : a.G; };
         for (int p = 0; p < a.nprob; ++p) {
             double w = (double)a.in[p].n2 * (double)a.in[p].n2 / tot;
-            cnt[p] = 1 + (int)(w * extra);
+            cnt[p] = min(cap_of(p, a.in[p].cap_wide), 1 + (int)(w * extra));
             given += cnt[p];
         }
-        for (int p = 0; given < a.G; p = (p + 1) % a.nprob) { cnt[p]++; given++; }
-        int acc = 0;
-        for (int p = 0; p < a.nprob; ++p) { plan->grp_first[p] = acc; acc += cnt[p]; }
+        for (bool grew = true; given < a.G && grew;) {
+            grew = false;
+            for (int p = 0; p < a.nprob && given < a.G; ++p)
+                if (cnt[p] < cap_of(p, a.in[p].cap_wide)) { cnt[p]++; given++; grew = true; }
+        }
+        int acc = 0, accn = 0;
+        for (int p = 0; p < a.nprob; ++p) {
+            plan->grp_first[p] = acc;
+            acc += cnt[p];
+            plan->grpn_first[p] = accn;
+            accn += min(cnt[p], cap_of(p, a.in[p].cap_narrow));
+        }
         plan->grp_first[a.nprob] = acc;
+        plan->grpn_first[a.nprob] = accn;
         long long di = 0, ai = 0;
         for (int p = 0; p < a.nprob; ++p) {
             plan->dom_item_start[p] = di;
-            di += dom_items_of(a.in[p].n2);
+            di += dom_items_of(a.in[p].n2, a.in[p].dom_chunk);
             plan->asc_item_start[p] = ai;
             if (a.in[p].mode == MODE_SELECT) ai += cdiv(a.in[p].n2, kAscPointsPerItem);
         }
@@ -106,7 +120,8 @@ __global__ void k_prep(Plan* plan)
 // Lexicographic order, sorted objective keys and runs of equal points.
 __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
 {
-    const Group g = group_of(plan);
+    const Group g = group_of(plan, false);
+    if (g.prob < 0) return;  // a CTA beyond every problem's group
     const ProbDev& d = plan->p[g.prob];
     const ProbIn& in = d.in;
     const long long budget = plan->spin_budget;

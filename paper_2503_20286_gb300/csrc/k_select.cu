@@ -47,7 +47,8 @@ __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned
 // Ideal point, ASF extreme points, nadir point, intercepts (Algorithm S.5).
 __global__ void __launch_bounds__(kCoopThreads, 1) k_stats(Plan* plan)
 {
-    const Group g = group_of(plan);
+    const Group g = group_of(plan, false);
+    if (g.prob < 0) return;  // a CTA beyond every problem's group
     const ProbDev& d = plan->p[g.prob];
     const ProbIn& in = d.in;
     const long long budget = plan->spin_budget;

@@ -33,27 +33,33 @@ int main()
             long long first_col_block = (rb * 32 + 1) / kColBlock;  // block of column p+1 for the first row
             if (rb / 32 > first_col_block) return fail("unstored tile with pairs", rb, first_col_block);
         }
-        // work items cover every (row block, column block) pair of the triangle once
-        std::vector<int> seen(idx, 0);
-        long long items = 0;
-        for (long long cb = 0; cb < ncb; ++cb) {
-            long long n = dom_items_of_cb(cb, nrb);
-            long long rbmax = nrb < 32 * (cb + 1) ? nrb : 32 * (cb + 1);
-            for (long long c = 0; c < n; ++c) {
-                for (long long rb = c * kDomRowChunk; rb < rbmax && rb < (c + 1) * kDomRowChunk; ++rb)
-                    seen[tile_index(rb, cb, ncb)] += 1;
-                ++items;
+        // work items cover every (row block, column block) pair of the triangle
+        // once, for every item size
+        for (long long chunk = kDomChunkMin; chunk <= kDomRowChunk; chunk *= 2) {
+            if (!dom_chunk_ok(chunk)) return fail("dom_chunk_ok", chunk, 1);
+            std::vector<int> seen(idx, 0);
+            long long items = 0;
+            for (long long cb = 0; cb < ncb; ++cb) {
+                long long n = dom_items_of_cb(cb, nrb, chunk);
+                long long rbmax = nrb < 32 * (cb + 1) ? nrb : 32 * (cb + 1);
+                for (long long c = 0; c < n; ++c) {
+                    for (long long rb = c * chunk; rb < rbmax && rb < (c + 1) * chunk; ++rb)
+                        seen[tile_index(rb, cb, ncb)] += 1;
+                    ++items;
+                }
             }
+            if (items != dom_items_of(n2, chunk)) return fail("dom_items_of", items, dom_items_of(n2, chunk));
+            // closed-form item prefix against the per-block sum
+            long long pre = 0;
+            for (long long cb = 0; cb <= ncb; ++cb) {
+                if (dom_items_prefix(cb, nrb, chunk) != pre)
+                    return fail("dom_items_prefix", dom_items_prefix(cb, nrb, chunk), pre);
+                if (cb < ncb) pre += dom_items_of_cb(cb, nrb, chunk);
+            }
+            for (long long t = 0; t < idx; ++t)
+                if (seen[t] != 1) return fail("tile coverage", t, seen[t]);
         }
-        if (items != dom_items_of(n2)) return fail("dom_items_of", items, dom_items_of(n2));
-        // closed-form item prefix against the per-block sum
-        long long pre = 0;
-        for (long long cb = 0; cb <= ncb; ++cb) {
-            if (dom_items_prefix(cb, nrb) != pre) return fail("dom_items_prefix", dom_items_prefix(cb, nrb), pre);
-            if (cb < ncb) pre += dom_items_of_cb(cb, nrb);
-        }
-        for (long long t = 0; t < idx; ++t)
-            if (seen[t] != 1) return fail("tile coverage", t, seen[t]);
+        if (dom_chunk_ok(32) || dom_chunk_ok(96) || dom_chunk_ok(2048)) return fail("dom_chunk_ok", 0, 0);
         // workspace: regions are 256-byte aligned, disjoint and inside the size
         for (int mode = MODE_RANK; mode <= MODE_SELECT; ++mode) {
             ProbIn in{};

@@ -68,6 +68,8 @@ def test_host_argument_checks_reject_before_launch(lib):
     assert L.emo_hype_select(p, 10, 3, p, None, 100, 5, p, None, None, p, 1 << 20, None) == 1        # no samples
     assert L.emo_autotune(3, 10, None) == 1                                                          # n2 < 64
     assert L.emo_autotune(1, 1000, None) == 1                                                        # m < 2
+    assert L.emo_launch_shape(3, 1000, None) == 1                                                    # no output
+    assert L.emo_launch_shape(17, 1000, p) == 1                                                      # m > 16
     assert L.emo_get_last_device_status(None, None) == 1
     assert L.emo_hype_select(p, 10, 3, p, p, 0, 5, p, None, None, p, 1 << 20, None) == 1           # s = 0
     assert L.emo_workspace_size(2, 0, 3, 5) == 0
@@ -86,9 +88,10 @@ def test_host_argument_checks_reject_before_launch(lib):
     assert mo(10, 4, 3, 2, -1.0, p, 1 << 20) == 1                       # theta < 0
     assert mo(10, 4, 3, 2, float("nan"), p, 1 << 20) == 1               # theta NaN
     assert mo(10, 4, 3, 2, 5.0, ctypes.c_void_p(128), 1 << 20) == 1     # workspace not 256-byte aligned
-    assert mo(100, 4, 3, 10, 5.0, p, 9983) == 3                         # one byte short
-    # regions: status + z_min keys (256), best value 8n, lowest index 4n, pair values 8nT, each 256-aligned
-    assert L.emo_workspace_size(4, 100, 3, 10) == 9984
+    assert mo(100, 4, 3, 10, 5.0, p, 14079) == 3                        # one byte short
+    # regions: status + z_min keys (256), best value 8n, lowest index 4n, pair values 8nT, per-subproblem
+    # ||w||, own value and unit weights 8n(m + 2), each 256-aligned
+    assert L.emo_workspace_size(4, 100, 3, 10) == 14080
     assert L.emo_workspace_size(4, 100, 3, 0) == 0
     assert L.emo_workspace_size(4, 100, 3, 101) == 0
     # generation operators
