@@ -72,3 +72,19 @@ def test_hype_larger_population():
     F = wl.population(20000, 3, 12, "sphere", seed=44)
     U = np.random.default_rng(9).random((3000, 3)).astype(np.float32)
     compare(F, np.full(3, 2.5, np.float32), U, 10000)
+
+
+@pytest.mark.parametrize("m,quant", [(5, 8.0), (8, None), (12, 4.0), (16, None)])
+def test_hype_many_objectives_and_ties(m, quant):
+    """Prefix sets with checkpoints every 2 to 16 columns (m >= 5), several
+    column blocks and, on a coarse grid, samples that tie point values in
+    single objectives (weak dominance: ties count)."""
+    F = wl.population(2600, m, m + 4, "sphere", seed=300 + m, quantize=quant)
+    rng = np.random.default_rng(m)
+    U = rng.random((1500, m)).astype(np.float32)
+    v_ref = (F.max(axis=0) * 1.05 + 0.02).astype(np.float32)
+    if quant:  # samples on the same grid as the points
+        lo = F.min(axis=0)
+        S_grid = np.round((lo + U * (v_ref - lo)) * quant) / quant
+        U = np.clip((S_grid - lo) / (v_ref - lo), 0.0, np.nextafter(np.float32(1), np.float32(0))).astype(np.float32)
+    compare(F, v_ref, U, 1300)
