@@ -213,15 +213,17 @@ def hype_timing(emo, torch, Ft, F, n_keep, flush, stream, steps, n_samples: int 
         a.record(stream)
         emo.emo_hype_select(Ft, vt, Ut, n_keep, survivors=surv, ws=ws)
         b.record(stream)
-        hype.append(dict(emo.emo_stage_times()).get("hype", float("nan")))
+        hype.append({k: v for k, v in emo.emo_stage_times() if k.startswith("hype")})
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
     emo.emo_set_stage_timing(False)
     if emo.emo_workspace_status(ws) != 0:
         raise SystemExit("HypE selection failed on the device")
     t = statistics.mean(ms)
+    parts = {k: statistics.mean(h[k] for h in hype) for k in hype[0]}
     return {"selection": "TensorHypE (Algorithms S.10, S.11)", "samples": n_samples, "steps": steps,
-            "ms_per_step": t, "selections_per_s": 1e3 / t, "hype_stage_ms": statistics.mean(hype)}
+            "ms_per_step": t, "selections_per_s": 1e3 / t, "hype_stage_ms": sum(parts.values()),
+            "hype_parts_ms": parts}
 
 
 def moead_inputs(h: int, m: int, d: int, t: int, seed: int):
@@ -425,6 +427,129 @@ def generation_loop(emo, torch, dev, flush, stream, gens: int = 20, n: int = N2 
             "igd_front": f"Das-Dennis H={H} directions projected onto the unit sphere",
             "last_info": dict(zip(("status", "last_rank", "n_before", "n_last", "fallback_used", "n_recheck",
                                    "n_fronts", "n_levels"), info.cpu().tolist()))}
+
+
+def batched_sharded(emo, torch, dev, world: int, rank: int, rounds: int = 5):
+    """The 64-population batch spread over the ranks (shard_populations:
+    longest first to the least-loaded rank, load (2N)^2), each rank's share
+    one emo_nsga3_select_batch call replayed from a CUDA graph; no
+    collective on the data path. Whole-job time = the slowest rank's."""
+    import torch.distributed as dist
+    from paper_2503_20286_gb300 import workloads as wl
+    from paper_2503_20286_gb300.replicas import max_over_ranks, shard_populations
+    probs = wl.config(3)
+    mine = shard_populations([p.n2 for p in probs], world)[rank]
+    items = []
+    for i in mine:
+        p = probs[i]
+        items.append({"F": torch.from_numpy(p.F).to(dev), "R": torch.from_numpy(p.R).to(dev), "n_keep": p.n_keep,
+                      "seed": p.seed, "generation": p.generation,
+                      "survivors": torch.empty(p.n_keep, dtype=torch.int32, device=dev)})
+    ms = 0.0
+    if items:
+        bws = torch.empty(emo.emo_batch_workspace_size(items), dtype=torch.uint8, device=dev)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            emo.emo_nsga3_select_batch(items, ws=bws, stream=side)
+        side.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            emo.emo_nsga3_select_batch(items, ws=bws, stream=side)
+        graph.replay()
+        torch.cuda.synchronize()
+        if emo.emo_workspace_status(bws) != 0:
+            raise RuntimeError("batched selection failed on the device")
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if items:
+        stream = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(rounds):
+            graph.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / rounds
+    if world > 1:
+        dist.barrier()
+    t = max_over_ranks(ms, dev)
+    pairs = float(sum(p.n2 * p.n2 for p in probs))
+    return {"populations": len(probs), "ranks": world, "populations_this_rank": len(mine), "ms": t,
+            "populations_per_s": len(probs) * 1e3 / t, "pairs_per_s": pairs * 1e3 / t, "scaling": "strong",
+            "split": "shard_populations (longest first, load (2N)^2), one batched graph replay per rank"}
+
+
+def autotune_report(emo, torch, dev, flush, stream, steps):
+    """Tuned against default launch shapes: workload 1 (2N = 20,000, M = 3:
+    one selection, and non-dominated sorting of every front) and the
+    64-population batch (one graph replay), timed before and after
+    emo_autotune has tuned every (m, size) they contain. Tuning runs offline,
+    outside every timed region; survivors must not change."""
+    from paper_2503_20286_gb300 import workloads as wl
+    p1 = wl.config(1)
+    F1, R1 = torch.from_numpy(p1.F).to(dev), torch.from_numpy(p1.R).to(dev)
+    probs = wl.config(3)
+    items = [{"F": torch.from_numpy(p.F).to(dev), "R": torch.from_numpy(p.R).to(dev), "n_keep": p.n_keep,
+              "seed": p.seed, "generation": p.generation,
+              "survivors": torch.empty(p.n_keep, dtype=torch.int32, device=dev)} for p in probs]
+    bws = torch.empty(emo.emo_batch_workspace_size(items), dtype=torch.uint8, device=dev)
+    ws1 = torch.empty(emo.emo_workspace_size(emo.EMO_OP_NSGA3_SELECT, p1.n2, p1.m, p1.n_r), dtype=torch.uint8,
+                      device=dev)
+    wsr = torch.empty(emo.emo_workspace_size(emo.EMO_OP_ND_RANK, p1.n2, p1.m, 0), dtype=torch.uint8, device=dev)
+    surv1 = torch.empty(p1.n_keep, dtype=torch.int32, device=dev)
+    rank1 = torch.empty(p1.n2, dtype=torch.int32, device=dev)
+
+    def timed(call):
+        for g in range(2):
+            call(g)
+        ms = []
+        for k in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            call(2 + k)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    def measure():
+        out = {"select_ms": timed(lambda g: emo.emo_nsga3_select(F1, R1, p1.n_keep, p1.seed, 0, survivors=surv1,
+                                                                 ws=ws1, stream=stream)),
+               "nd_rank_all_fronts_ms": timed(lambda g: emo.emo_nd_rank(F1, 0, rank=rank1, ws=wsr, stream=stream))}
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            emo.emo_nsga3_select_batch(items, ws=bws, stream=side)
+        side.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            emo.emo_nsga3_select_batch(items, ws=bws, stream=side)
+        torch.cuda.synchronize()
+        out["batch_64_graph_ms"] = timed(lambda g: graph.replay())
+        out["shape_workload_1"] = emo.emo_launch_shape(p1.m, p1.n2)
+        return out, surv1.clone(), rank1.clone(), [it["survivors"].clone() for it in items]
+
+    emo.emo_autotune_reset()
+    default, s_d, r_d, b_d = measure()
+    t0 = time.perf_counter()
+    tuned_keys = sorted({(p1.m, p1.n2.bit_length())} | {(p.m, p.n2.bit_length()) for p in probs})
+    done = set()
+    for m, n2 in [(p1.m, p1.n2)] + [(p.m, p.n2) for p in probs]:
+        if (m, n2.bit_length()) not in done:
+            emo.emo_autotune(m, n2)
+            done.add((m, n2.bit_length()))
+    tune_s = time.perf_counter() - t0
+    tuned, s_t, r_t, b_t = measure()
+    emo.emo_autotune_reset()  # the rest of the bench runs with the default shapes
+    same = bool(torch.equal(s_d, s_t) and torch.equal(r_d, r_t) and all(torch.equal(a, b) for a, b in zip(b_d, b_t)))
+    return {"default": default, "tuned": tuned, "tuned_sizes": len(tuned_keys), "tune_s": tune_s,
+            "speedup": {k: default[k] / tuned[k] for k in ("select_ms", "nd_rank_all_fronts_ms", "batch_64_graph_ms")},
+            "survivors_and_ranks_identical": same,
+            "tuner": "emo_autotune: dominance item size, peel CTAs per front, other cooperative CTAs, association "
+                     "blocks per SM (coordinate search, best of three)"}
 
 
 def _gpu_select_debug(emo, torch, dev, F, R, n_keep, seed, gen):
@@ -721,6 +846,13 @@ def main():
             line["generation_loop"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and not args.no_batch:
         line["batched_vs_plain"] = batched_vs_plain(emo, torch, dev)
+    if not args.no_batch:
+        line["batched_sharded"] = batched_sharded(emo, torch, dev, world, rank)
+    if rank == 0 and world == 1 and not args.no_batch:
+        try:
+            line["autotune"] = autotune_report(emo, torch, dev, flush, stream, max(5, args.steps))
+        except Exception as e:  # reported in the line; the selection numbers above stand
+            line["autotune"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, nr_s = oracle_time(F, R, n_keep, seed, SAMPLE_N2)
         line["cpu_baseline"] = {"value": SAMPLE_N2 ** 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -99,7 +99,8 @@ typedef enum {
     EMO_OP_NSGA3_SELECT = 2,
     EMO_OP_HYPE_SELECT = 3,
     EMO_OP_MOEAD_SELECT = 4, /* emo_workspace_size(EMO_OP_MOEAD_SELECT, n, m, T) */
-    EMO_OP_IGD = 5           /* emo_workspace_size(EMO_OP_IGD, n_ref, m, 0) */
+    EMO_OP_IGD = 5,          /* emo_workspace_size(EMO_OP_IGD, n_ref, m, 0) */
+    EMO_OP_SELECT_RANKED = 6 /* emo_nsga3_select_ranked (no dominance matrix) */
 } emo_op;
 
 /* Front shapes of the stand-in objective functions (emo_standin_objectives). */
@@ -124,6 +125,29 @@ size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r);
  */
 emo_status emo_dominance(const float* F, int64_t n2, int32_t m, uint32_t* D, int64_t ld_words,
                          int32_t* dom_count, emo_stream_t stream);
+
+/*
+ * emo_dominance restricted to the columns [col_lo, col_hi) (col_lo a multiple
+ * of 1024, col_hi <= n2): row i (all n2 rows), word w, bit b of D is 1 iff
+ * F_i dominates F_{col_lo + 32w + b}; ld_words >= ceil((col_hi - col_lo) / 32);
+ * dom_count[j - col_lo] (nullable) = the dominators of column j. One rank's
+ * share of the matrix when the columns of one population are split over
+ * several GPUs (each GPU holds D[:, its columns]).
+ */
+emo_status emo_dominance_cols(const float* F, int64_t n2, int32_t m, int64_t col_lo, int64_t col_hi, uint32_t* D,
+                              int64_t ld_words, int32_t* dom_count, emo_stream_t stream);
+
+/*
+ * One peeling step (Algorithm S.3, "c -= d") on a rank's columns: with D as
+ * written by emo_dominance_cols (ncols columns, leading dimension ld_words),
+ * counts[j] -= the number of the n_rows rows listed in `rows` (device int32,
+ * row indices of the current front) whose bit j is set, and next_front[j]
+ * (device uint8) = 1 when counts[j] reached zero in this step, else 0. The
+ * rows of one front never dominate each other, so a column of the current
+ * front is never flagged again.
+ */
+emo_status emo_front_counts(const uint32_t* D, int64_t ld_words, int64_t ncols, const int32_t* rows, int64_t n_rows,
+                            int32_t* counts, uint8_t* next_front, emo_stream_t stream);
 
 /*
  * Nondominated sorting (Section IV-A "Nondominated Sorting", Algorithm S.3,
@@ -182,6 +206,22 @@ emo_status emo_nsga3_select_ex(const float* F, int64_t n2, int32_t m, const floa
                                int64_t n_keep, uint64_t seed, uint64_t generation, int32_t niche_mode,
                                int32_t* survivors, emo_select_info* info, const emo_select_debug* dbg,
                                void* ws, size_t ws_bytes, emo_stream_t stream);
+
+/*
+ * emo_nsga3_select for a population whose nondominated ranks are already
+ * known (computed, for instance, by several GPUs that split the columns of
+ * its dominance matrix): rank is device int32 [n2] in caller order, 0-based
+ * fronts for at least the first n_keep points of the order by rank, and
+ * EMO_NOT_RANKED (or any rank) beyond. l, |P| and |L| follow from the ranks;
+ * normalisation, association, niching and survivors are those of
+ * emo_nsga3_select. No dominance matrix is built: ws of
+ * emo_workspace_size(EMO_OP_SELECT_RANKED, n2, m, n_r) bytes. Fewer than
+ * n_keep ranked points gives EMO_ERR_INVALID_ARG on the device.
+ */
+emo_status emo_nsga3_select_ranked(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
+                                   int64_t n_keep, uint64_t seed, uint64_t generation, const int32_t* rank,
+                                   int32_t* survivors, emo_select_info* info, void* ws, size_t ws_bytes,
+                                   emo_stream_t stream);
 
 /* As emo_nsga3_select, also writing the intermediates named in `dbg` (a
  * host pointer to a struct of device pointers, nullable). */
@@ -365,17 +405,20 @@ emo_status emo_get_last_device_status(emo_stream_t stream, int32_t* status_out);
  * simplex), each candidate the best of three selections, in this order:
  *   1. dominance work-item size (row blocks per item: 64 .. 1024) by the
  *      dominance kernel's time;
- *   2. the per-front schedule of the peeling: how many CTAs serve a front
- *      (every CTA, half, a quarter, ... down to a single CTA, whose fronts
- *      then need no grid barrier) by the peeling time;
+ *   2. the schedule of the peeling by its time: one grid barrier per front,
+ *      or the wavefront (a block's task for front k starts as soon as every
+ *      lower column block has finished front k - 1; no grid barrier); then
+ *      how many CTAs serve it (every CTA, half, a quarter, ... down to a
+ *      single CTA);
  *   3. the CTAs of the other cooperative stages (sort, statistics, CSR,
  *      niching, survivors; at most as many as step 2) by their summed time;
  *   4. the association kernel's blocks per SM (2, 4, 8, 16, 32).
  * It allocates device memory and synchronises, so it belongs outside timed
  * regions and graph captures. With a non-null `cache_path`, results found in
  * that text file (lines "arch m bucket assoc_bps dom_chunk cap_wide
- * cap_narrow", arch = 10 * major + minor compute capability, bucket =
- * floor(log2 n2), a cap of 0 = every CTA) are loaded and reused, and a new
+ * cap_narrow peel_wave", arch = 10 * major + minor compute capability,
+ * bucket = floor(log2 n2), a cap of 0 = every CTA; lines of the first four
+ * or seven fields also load) are loaded and reused, and a new
  * result is appended. Later calls of the same process use the tuned shapes,
  * and the first selection of a process loads the file named by the
  * environment variable EMO_AUTOTUNE_CACHE, if set. Untuned sizes use 8
@@ -385,10 +428,11 @@ emo_status emo_get_last_device_status(emo_stream_t stream, int32_t* status_out);
 emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path);
 
 /* The launch shapes a selection of n2 points with m objectives would use on
- * the current device now (tuned or default): shape_out[0] association
- * blocks per SM, [1] dominance row blocks per work item, [2] CTAs of the
- * peeling group, [3] CTAs of the other cooperative groups (a batch can give
- * a population fewer). */
+ * the current device now (tuned or default), into shape_out[5]: [0]
+ * association blocks per SM, [1] dominance row blocks per work item, [2]
+ * CTAs of the peeling group, [3] CTAs of the other cooperative groups (a
+ * batch can give a population fewer), [4] the peeling schedule (1
+ * wavefront, 0 a grid barrier per front). */
 emo_status emo_launch_shape(int32_t m, int64_t n2, int32_t* shape_out);
 
 /* Forgets every tuned shape of this process (later calls use the defaults

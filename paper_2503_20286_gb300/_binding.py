@@ -19,7 +19,8 @@ from . import build as _build
 EMO_OK = 0
 STATUS_NAMES = {0: "EMO_OK", 1: "EMO_ERR_INVALID_ARG", 2: "EMO_ERR_NONFINITE", 3: "EMO_ERR_WORKSPACE",
                 4: "EMO_ERR_CUDA", 5: "EMO_ERR_TIMEOUT", 6: "EMO_ERR_NOT_IMPLEMENTED"}
-EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT, EMO_OP_HYPE_SELECT, EMO_OP_MOEAD_SELECT, EMO_OP_IGD = range(6)
+EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT, EMO_OP_HYPE_SELECT, EMO_OP_MOEAD_SELECT, EMO_OP_IGD, \
+    EMO_OP_SELECT_RANKED = range(7)
 EMO_SHAPE_LINEAR, EMO_SHAPE_SPHERE = 0, 1
 EMO_NOT_RANKED = 2147483647
 EMO_NICHE_EXACT, EMO_NICHE_ONESHOT = 0, 1
@@ -79,6 +80,12 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             L.emo_workspace_size.argtypes = [ctypes.c_int, i64, i32, i32]
             L.emo_dominance.restype = ctypes.c_int
             L.emo_dominance.argtypes = [vp, i64, i32, vp, i64, vp, vp]
+            L.emo_dominance_cols.restype = ctypes.c_int
+            L.emo_dominance_cols.argtypes = [vp, i64, i32, i64, i64, vp, i64, vp, vp]
+            L.emo_front_counts.restype = ctypes.c_int
+            L.emo_front_counts.argtypes = [vp, i64, i64, vp, i64, vp, vp, vp]
+            L.emo_nsga3_select_ranked.restype = ctypes.c_int
+            L.emo_nsga3_select_ranked.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp, vp, vp, sz, vp]
             L.emo_nd_rank.restype = ctypes.c_int
             L.emo_nd_rank.argtypes = [vp, i64, i32, i64, vp, vp, vp, sz, vp]
             L.emo_nsga3_select.restype = ctypes.c_int
@@ -182,6 +189,50 @@ def emo_dominance(F: torch.Tensor, D: torch.Tensor | None = None, dom_count: tor
     _check(lib().emo_dominance(_ptr(F), n2, m, _ptr(D), D.shape[1], _ptr(dom_count), _stream(stream)),
            "emo_dominance")
     return D, dom_count
+
+
+def emo_dominance_cols(F: torch.Tensor, col_lo: int, col_hi: int, D: torch.Tensor | None = None,
+                       dom_count: torch.Tensor | None = None, stream=None):
+    """Columns [col_lo, col_hi) of the dominance matrix (every row) and their
+    dominator counts; col_lo a multiple of 1024."""
+    n2, m = F.shape
+    ncols = col_hi - col_lo
+    if D is None:
+        D = torch.empty((n2, (ncols + 31) // 32), dtype=torch.int32, device=F.device)
+    if dom_count is None:
+        dom_count = torch.empty(ncols, dtype=torch.int32, device=F.device)
+    _check(lib().emo_dominance_cols(_ptr(F), n2, m, int(col_lo), int(col_hi), _ptr(D), D.shape[1], _ptr(dom_count),
+                                    _stream(stream)), "emo_dominance_cols")
+    return D, dom_count
+
+
+def emo_front_counts(D: torch.Tensor, ncols: int, rows: torch.Tensor, counts: torch.Tensor,
+                     next_front: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """One peeling step on a rank's columns: counts -= rows' bits; returns
+    the uint8 flags of the columns whose count reached zero."""
+    if next_front is None:
+        next_front = torch.empty(ncols, dtype=torch.uint8, device=D.device)
+    _check(lib().emo_front_counts(_ptr(D), D.shape[1], int(ncols), _ptr(rows) if rows.numel() else None,
+                                  rows.numel(), _ptr(counts), _ptr(next_front), _stream(stream)), "emo_front_counts")
+    return next_front
+
+
+def emo_nsga3_select_ranked(F: torch.Tensor, R: torch.Tensor, n_keep: int, seed: int, generation: int,
+                            rank: torch.Tensor, survivors: torch.Tensor | None = None, info: torch.Tensor | None = None,
+                            ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Selection of a population whose ranks are given (no dominance matrix)."""
+    n2, m = F.shape
+    n_r = R.shape[0]
+    if survivors is None:
+        survivors = torch.empty(n_keep, dtype=torch.int32, device=F.device)
+    nbytes = emo_workspace_size(EMO_OP_SELECT_RANKED, n2, m, n_r)
+    if nbytes == 0:
+        raise EmoError(1, "emo_workspace_size")
+    ws = _ws(nbytes, ws, F.device)
+    _check(lib().emo_nsga3_select_ranked(_ptr(F), n2, m, _ptr(R), n_r, n_keep, seed & 0xFFFFFFFFFFFFFFFF,
+                                         generation & 0xFFFFFFFFFFFFFFFF, _ptr(rank), _ptr(survivors), _ptr(info),
+                                         _ptr(ws), nbytes, _stream(stream)), "emo_nsga3_select_ranked")
+    return survivors
 
 
 def emo_nd_rank(F: torch.Tensor, n_keep: int = 0, rank: torch.Tensor | None = None,
@@ -387,10 +438,10 @@ def emo_workspace_status(ws: torch.Tensor, stream=None) -> int:
 
 def emo_launch_shape(m: int, n2: int) -> dict:
     """Launch shapes a selection of (n2, m) uses now on the current device."""
-    out = (ctypes.c_int32 * 4)()
+    out = (ctypes.c_int32 * 5)()
     _check(lib().emo_launch_shape(int(m), int(n2), ctypes.addressof(out)), "emo_launch_shape")
     return {"assoc_blocks_per_sm": out[0], "dom_rowblocks_per_item": out[1], "peel_ctas": out[2],
-            "other_coop_ctas": out[3]}
+            "other_coop_ctas": out[3], "peel_wavefront": out[4]}
 
 
 def emo_autotune_reset() -> None:

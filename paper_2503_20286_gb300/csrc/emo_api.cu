@@ -23,6 +23,7 @@ namespace {
 
 std::atomic<long long> g_spin_budget{0};
 constexpr int kPeelDynSmem = peel_smem_bytes((int)(kMaxN2 / kColBlock));
+constexpr int kPeelWaveDynSmem = peel_wave_smem_bytes((int)(kMaxN2 / kColBlock));
 std::atomic<int> g_timing{0};
 
 // Per-thread stage timing of the last run() (opt-in; events on the launch stream).
@@ -97,14 +98,19 @@ DevInfo dev_info()
         if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
             return DevInfo{};
         if (cudaFuncSetAttribute((const void*)k_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeelDynSmem) !=
-            cudaSuccess)
+                cudaSuccess ||
+            cudaFuncSetAttribute((const void*)k_peel_wave, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kPeelWaveDynSmem) != cudaSuccess ||
+            cudaFuncSetAttribute((const void*)k_hype_counts, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 hype_counts_smem(4)) != cudaSuccess)
             return DevInfo{};
         int occ = 2;
         // k_peel takes peel_smem_bytes(ncb) of dynamic shared memory, the others none
-        const void* kernels[] = {(const void*)k_sort, (const void*)k_peel,  (const void*)k_stats,
-                                 (const void*)k_csr,  (const void*)k_niche, (const void*)k_niche_oneshot,
-                                 (const void*)k_hype, (const void*)k_finish};
-        const int dyn[] = {0, kPeelDynSmem, 0, 0, 0, 0, 0, 0};
+        const void* kernels[] = {(const void*)k_sort,  (const void*)k_peel,  (const void*)k_peel_wave,
+                                 (const void*)k_stats, (const void*)k_csr,   (const void*)k_niche,
+                                 (const void*)k_niche_oneshot, (const void*)k_hype, (const void*)k_finish,
+                                 (const void*)k_rank_in};
+        const int dyn[] = {0, kPeelDynSmem, kPeelWaveDynSmem, 0, 0, 0, 0, 0, 0, 0};
         for (int i = 0; i < (int)(sizeof(dyn) / sizeof(dyn[0])); ++i) {
             int o = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernels[i], kCoopThreads, dyn[i]) != cudaSuccess)
@@ -149,6 +155,11 @@ cudaError_t coop(const void* fn, int G, size_t smem, cudaStream_t s, Plan* plan)
     void* args[] = {&plan};
     return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCoopThreads), args, smem, s);
 }
+cudaError_t coop_phase(const void* fn, int G, size_t smem, cudaStream_t s, Plan* plan, int phase)
+{
+    void* args[] = {&plan, &phase};
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCoopThreads), args, smem, s);
+}
 
 // Launch shapes, per (compute capability as 10 * major + minor, m,
 // floor(log2 n2)); survivors never depend on them. emo_autotune measures
@@ -158,10 +169,12 @@ struct Shape {
     int dom_chunk;   // dominance: row blocks per work item (64 .. 1024, a power of two)
     int cap_wide;    // CTAs of the peeling / TensorHypE group of one problem (0 = no cap)
     int cap_narrow;  // CTAs of the other cooperative groups (0 = no cap)
+    int peel_wave;   // peeling schedule: 1 wavefront (no grid barrier per front), 0 one grid barrier per front
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, Shape> g_tune;
-Shape g_force{0, 0, -1, -1};  // set only while emo_autotune times a candidate (0 / -1 = not forced)
+Shape g_force{0, 0, -1, -1, -1};  // set only while emo_autotune times a candidate (0 / -1 = not forced)
+constexpr int kDefaultPeelWave = 0;
 
 int size_bucket(int64_t n2)
 {
@@ -179,7 +192,7 @@ int device_arch(int dev)
 }
 
 // Cache file: one line per tuned size, "arch m bucket assoc_bps" optionally
-// followed by "dom_chunk cap_wide cap_narrow".
+// followed by "dom_chunk cap_wide cap_narrow" and "peel_wave".
 void load_tune_cache(const char* path)
 {
     FILE* fh = path ? std::fopen(path, "r") : nullptr;
@@ -187,10 +200,13 @@ void load_tune_cache(const char* path)
     char line[256];
     std::lock_guard<std::mutex> lk(g_tune_mu);
     while (std::fgets(line, sizeof(line), fh)) {
-        int v[7] = {0, 0, 0, 0, kDomRowChunk, 0, 0};
-        const int n = std::sscanf(line, "%d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6]);
-        if ((n != 4 && n != 7) || v[3] < 1 || v[3] > 64 || !dom_chunk_ok(v[4]) || v[5] < 0 || v[6] < 0) continue;
-        g_tune[std::make_tuple(v[0], v[1], v[2])] = Shape{v[3], v[4], v[5], v[6]};
+        int v[8] = {0, 0, 0, 0, kDomRowChunk, 0, 0, kDefaultPeelWave};
+        const int n = std::sscanf(line, "%d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                                  &v[7]);
+        if ((n != 4 && n != 7 && n != 8) || v[3] < 1 || v[3] > 64 || !dom_chunk_ok(v[4]) || v[5] < 0 || v[6] < 0 ||
+            v[7] < 0 || v[7] > 1)
+            continue;
+        g_tune[std::make_tuple(v[0], v[1], v[2])] = Shape{v[3], v[4], v[5], v[6], v[7]};
     }
     std::fclose(fh);
 }
@@ -199,7 +215,7 @@ void load_tune_cache(const char* path)
 // that still give every SM two or more, no group caps.
 Shape default_shape(int sms, int64_t n2)
 {
-    Shape sh{8, kDomRowChunk, 0, 0};
+    Shape sh{8, kDomRowChunk, 0, 0, kDefaultPeelWave};
     while (sh.dom_chunk > kDomChunkMin && dom_items_of(n2, sh.dom_chunk) < 2ll * sms) sh.dom_chunk >>= 1;
     return sh;
 }
@@ -217,8 +233,45 @@ Shape shape_for(int dev, int sms, int m, int64_t n2)
         if (g_force.dom_chunk > 0) sh.dom_chunk = g_force.dom_chunk;
         if (g_force.cap_wide >= 0) sh.cap_wide = g_force.cap_wide;
         if (g_force.cap_narrow >= 0) sh.cap_narrow = g_force.cap_narrow;
+        if (g_force.peel_wave >= 0) sh.peel_wave = g_force.peel_wave;
     }
     return sh;
+}
+
+// The selection stages after the peeling (statistics, association, niche
+// counts, niching, survivors); with `finish`, also the survivors' stage.
+emo_status run_selection_stages(std::vector<ProbIn>& ins, const DevInfo& di, Plan* plan, int dev, cudaStream_t s,
+                                StageMarker& sm, bool finish = true)
+{
+    const int nprob = (int)ins.size();
+    if (coop((const void*)k_stats, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+    sm.mark("stats");
+    std::vector<int> m_of(nprob);
+    for (int p = 0; p < nprob; ++p) m_of[p] = ins[p].m;
+    int big = 0;
+    for (int p = 1; p < nprob; ++p)
+        if (ins[p].n2 > ins[big].n2) big = p;
+    const int bps = shape_for(dev, di.sms, ins[big].m, ins[big].n2).assoc_bps;
+    if (launch_assoc(plan, nprob, m_of.data(), di.sms, bps, s) != cudaSuccess) return EMO_ERR_CUDA;
+    sm.mark("assoc");
+    k_rescan<<<di.sms * 2, 256, 0, s>>>(plan);
+    if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
+    sm.mark("rescan");
+    if (coop((const void*)k_csr, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+    sm.mark("csr");
+    bool any_exact = false, any_oneshot = false;
+    for (const ProbIn& in : ins) {
+        any_exact |= in.mode == MODE_SELECT && in.niche == EMO_NICHE_EXACT;
+        any_oneshot |= in.mode == MODE_SELECT && in.niche == EMO_NICHE_ONESHOT;
+    }
+    if (any_exact && coop((const void*)k_niche, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+    if (any_oneshot && coop((const void*)k_niche_oneshot, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+    sm.mark("niche");
+    if (finish) {
+        if (coop((const void*)k_finish, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("finish");
+    }
+    return EMO_OK;
 }
 
 // Launch the whole pipeline for problems already laid out in `ins` (ordered
@@ -265,6 +318,11 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
     sm.mark("prep");
     if (coop((const void*)k_sort, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("sort");
+    if (nprob == 1 && ins[0].ranked) {  // the ranks are given: no dominance matrix, no peeling
+        if (coop((const void*)k_rank_in, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("rank_in");
+        return run_selection_stages(ins, di, plan, dev, s, sm);
+    }
     if (launch_colprep(plan, di.sms, s, nprob) != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("colprep");
     // dominance: one launch per objective count present
@@ -283,36 +341,30 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
         p = q;
     }
     sm.mark("dominance");
-    const size_t peel_smem = (size_t)peel_smem_bytes(max_ncb);
-    if (coop((const void*)k_peel, di.G, peel_smem, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
-    sm.mark("peel");
-    if (any_select) {
-        if (coop((const void*)k_stats, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
-        sm.mark("stats");
-        std::vector<int> m_of(nprob);
-        for (int p = 0; p < nprob; ++p) m_of[p] = ins[p].m;
+    {
         int big = 0;
         for (int p = 1; p < nprob; ++p)
             if (ins[p].n2 > ins[big].n2) big = p;
-        const int bps = shape_for(dev, di.sms, ins[big].m, ins[big].n2).assoc_bps;
-        if (launch_assoc(plan, nprob, m_of.data(), di.sms, bps, s) != cudaSuccess) return EMO_ERR_CUDA;
-        sm.mark("assoc");
-        k_rescan<<<di.sms * 2, 256, 0, s>>>(plan);
-        if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
-        sm.mark("rescan");
-        if (coop((const void*)k_csr, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
-        sm.mark("csr");
-        bool any_exact = false, any_oneshot = false;
-        for (const ProbIn& in : ins) {
-            any_exact |= in.mode == MODE_SELECT && in.niche == EMO_NICHE_EXACT;
-            any_oneshot |= in.mode == MODE_SELECT && in.niche == EMO_NICHE_ONESHOT;
-        }
-        if (any_exact && coop((const void*)k_niche, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
-        if (any_oneshot && coop((const void*)k_niche_oneshot, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
-        sm.mark("niche");
+        const bool wave = shape_for(dev, di.sms, ins[big].m, ins[big].n2).peel_wave != 0;
+        const size_t smem = (size_t)(wave ? peel_wave_smem_bytes(max_ncb) : peel_smem_bytes(max_ncb));
+        if (coop(wave ? (const void*)k_peel_wave : (const void*)k_peel, di.G, smem, s, plan) != cudaSuccess)
+            return EMO_ERR_CUDA;
+    }
+    sm.mark("peel");
+    if (any_select) {
+        const emo_status st = run_selection_stages(ins, di, plan, dev, s, sm, false);
+        if (st != EMO_OK) return st;
     }
     if (any_hype) {
-        if (coop((const void*)k_hype, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        int hm = 2;
+        for (const ProbIn& in : ins)
+            if (in.mode == MODE_HYPE) hm = std::max(hm, (int)in.m);
+        if (coop_phase((const void*)k_hype, di.G, 0, s, plan, 0) != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("hype_samples");
+        k_hype_counts<<<di.sms, kCoopThreads, hype_counts_smem(hm), s>>>(plan);
+        if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("hype_counts");
+        if (coop_phase((const void*)k_hype, di.G, 0, s, plan, 1) != cudaSuccess) return EMO_ERR_CUDA;
         sm.mark("hype");
     }
     if (coop((const void*)k_finish, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
@@ -366,6 +418,13 @@ size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r)
 {
     if (!sizes_ok(n2, m)) return 0;
     if (op == EMO_OP_DOMINANCE) return 0;
+    if (op == EMO_OP_SELECT_RANKED) {
+        if (n_r < 1) return 0;
+        ProbIn in = make_in(nullptr, nullptr, n2, m, n_r, n2, 0, 0, nullptr, nullptr, MODE_SELECT);
+        in.ranked = 1;
+        const int64_t b = problem_bytes(in);
+        return b < 0 ? 0 : (size_t)(kPlanBytes + b);
+    }
     if (op == EMO_OP_MOEAD_SELECT) return n_r >= 1 && n_r <= n2 ? (size_t)moead_layout(n2, m, n_r, nullptr, nullptr) : 0;
     if (op == EMO_OP_IGD) return (size_t)(n2 * 8);
     int mode = op == EMO_OP_ND_RANK ? MODE_RANK
@@ -379,22 +438,33 @@ size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r)
     return b < 0 ? 0 : (size_t)(kPlanBytes + b);
 }
 
-emo_status emo_dominance(const float* F, int64_t n2, int32_t m, uint32_t* D, int64_t ld_words, int32_t* dom_count,
-                         emo_stream_t stream)
+emo_status emo_dominance_cols(const float* F, int64_t n2, int32_t m, int64_t col_lo, int64_t col_hi, uint32_t* D,
+                              int64_t ld_words, int32_t* dom_count, emo_stream_t stream)
 {
-    if (!F || !D || !sizes_ok(n2, m) || ld_words < cdiv(n2, 32)) return EMO_ERR_INVALID_ARG;
+    if (!F || !D || !sizes_ok(n2, m) || col_lo < 0 || col_hi > n2 || col_lo >= col_hi || col_lo % kColBlock != 0 ||
+        ld_words < cdiv(col_hi - col_lo, 32))
+        return EMO_ERR_INVALID_ARG;
     if (!aligned(F, 4) || !aligned(D, 4) || (dom_count && !aligned(dom_count, 4))) return EMO_ERR_INVALID_ARG;
     DevInfo di = dev_info();
     if (!di.ok) return EMO_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    if (dom_count && cudaMemsetAsync(dom_count, 0, (size_t)n2 * 4, s) != cudaSuccess) return EMO_ERR_CUDA;
-    const int64_t wfull = cdiv(n2, kColBlock) * 32;
+    const int64_t ncols = col_hi - col_lo;
+    if (dom_count && cudaMemsetAsync(dom_count, 0, (size_t)ncols * 4, s) != cudaSuccess) return EMO_ERR_CUDA;
+    const int64_t wfull = cdiv(ncols, kColBlock) * 32;  // words the kernel writes per row
     if (ld_words > wfull &&
         cudaMemset2DAsync(D + wfull, (size_t)ld_words * 4, 0, (size_t)(ld_words - wfull) * 4, (size_t)n2, s) !=
             cudaSuccess)
         return EMO_ERR_CUDA;
-    if (launch_dominance_full_c(F, n2, m, D, ld_words, dom_count, di.sms, s) != cudaSuccess) return EMO_ERR_CUDA;
+    if (launch_dominance_full_c(F, n2, col_lo, col_hi, m, D, ld_words, dom_count, di.sms, s) != cudaSuccess)
+        return EMO_ERR_CUDA;
     return EMO_OK;
+}
+
+emo_status emo_dominance(const float* F, int64_t n2, int32_t m, uint32_t* D, int64_t ld_words, int32_t* dom_count,
+                         emo_stream_t stream)
+{
+    if (!F || !D || !sizes_ok(n2, m) || ld_words < cdiv(n2, 32)) return EMO_ERR_INVALID_ARG;
+    return emo_dominance_cols(F, n2, m, 0, n2, D, ld_words, dom_count, stream);
 }
 
 emo_status emo_nd_rank(const float* F, int64_t n2, int32_t m, int64_t n_keep, int32_t* rank, int32_t* last_rank,
@@ -549,6 +619,35 @@ emo_status emo_nsga3_select_ex(const float* F, int64_t n2, int32_t m, const floa
     ins[0].niche = niche_mode;
     if (dbg) ins[0].dbg = *dbg;
     return run(ins, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+emo_status emo_nsga3_select_ranked(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
+                                   int64_t n_keep, uint64_t seed, uint64_t generation, const int32_t* rank,
+                                   int32_t* survivors, emo_select_info* info, void* ws, size_t ws_bytes,
+                                   emo_stream_t stream)
+{
+    emo_status st = check_select_args(F, n2, m, R, n_r, n_keep, survivors);
+    if (st != EMO_OK) return st;
+    if (!rank || !aligned(rank, 4)) return EMO_ERR_INVALID_ARG;
+    std::vector<ProbIn> ins(1, make_in(F, R, n2, m, n_r, n_keep, seed, generation, survivors, info, MODE_SELECT));
+    ins[0].ranked = 1;
+    ins[0].rank_in = rank;
+    return run(ins, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+emo_status emo_front_counts(const uint32_t* D, int64_t ld_words, int64_t ncols, const int32_t* rows, int64_t n_rows,
+                            int32_t* counts, uint8_t* next_front, emo_stream_t stream)
+{
+    if (!D || !counts || !next_front || ncols < 1 || ncols > kMaxN2 || ld_words < cdiv(ncols, 32) || n_rows < 0 ||
+        n_rows > kMaxN2 || (n_rows > 0 && !rows))
+        return EMO_ERR_INVALID_ARG;
+    if (!aligned(D, 4) || !aligned(counts, 4) || (rows && !aligned(rows, 4))) return EMO_ERR_INVALID_ARG;
+    DevInfo di = dev_info();
+    if (!di.ok) return EMO_ERR_CUDA;
+    return launch_front_counts(D, ld_words, ncols, rows, n_rows, counts, next_front, di.sms, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? EMO_OK
+               : EMO_ERR_CUDA;
 }
 
 emo_status emo_nsga3_select_debug(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
@@ -710,6 +809,13 @@ emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path)
             const float v = timed(t, {"dominance"});
             if (v < bms) { bms = v; best.dom_chunk = c; }
         }
+        bms = INFINITY;
+        for (int w = 0; w <= 1 && st == EMO_OK; ++w) {
+            Shape t = best;
+            t.peel_wave = w;
+            const float v = timed(t, {"peel"});
+            if (v < bms) { bms = v; best.peel_wave = w; }
+        }
         std::vector<int> caps = {0};
         for (int c = di.G / 2; c >= 1; c /= 2) caps.push_back(c);
         bms = INFINITY;
@@ -740,7 +846,7 @@ emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path)
         }
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_force = Shape{0, 0, -1, -1};
+            g_force = Shape{0, 0, -1, -1, -1};
         }
         g_timing.store(prev_timing);
     }
@@ -752,8 +858,8 @@ emo_status emo_autotune(int32_t m, int64_t n2, const char* cache_path)
     }
     if (cache_path)
         if (FILE* fh = std::fopen(cache_path, "a")) {
-            std::fprintf(fh, "%d %d %d %d %d %d %d\n", arch, (int)m, size_bucket(n2), best.assoc_bps, best.dom_chunk,
-                         best.cap_wide, best.cap_narrow);
+            std::fprintf(fh, "%d %d %d %d %d %d %d %d\n", arch, (int)m, size_bucket(n2), best.assoc_bps,
+                         best.dom_chunk, best.cap_wide, best.cap_narrow, best.peel_wave);
             std::fclose(fh);
         }
     return EMO_OK;
@@ -771,6 +877,7 @@ emo_status emo_launch_shape(int32_t m, int64_t n2, int32_t* shape_out)
     shape_out[1] = sh.dom_chunk;
     shape_out[2] = sh.cap_wide > 0 ? std::min(sh.cap_wide, di.G) : di.G;
     shape_out[3] = sh.cap_narrow > 0 ? std::min(sh.cap_narrow, shape_out[2]) : shape_out[2];
+    shape_out[4] = sh.peel_wave;
     return EMO_OK;
 }
 
@@ -811,7 +918,8 @@ int32_t emo_device_report(char* buf, int32_t len)
     const K ks[] = {{"k_sort", (const void*)k_sort, 0}, {"k_peel", (const void*)k_peel, kPeelDynSmem},
                     {"k_stats", (const void*)k_stats, 0}, {"k_csr", (const void*)k_csr, 0},
                     {"k_niche", (const void*)k_niche, 0}, {"k_niche_oneshot", (const void*)k_niche_oneshot, 0},
-                    {"k_hype", (const void*)k_hype, 0},
+                    {"k_peel_wave", (const void*)k_peel_wave, kPeelWaveDynSmem},
+                    {"k_hype", (const void*)k_hype, 0}, {"k_hype_counts", (const void*)k_hype_counts, hype_counts_smem(4)},
                     {"k_finish", (const void*)k_finish, 0}};
     for (const K& k : ks) {
         cudaFuncAttributes fa{};

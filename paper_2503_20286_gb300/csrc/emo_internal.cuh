@@ -70,7 +70,8 @@ struct ProbIn {
     int32_t dom_chunk;       // row blocks per dominance work item: 64 .. 1024, a power of two
     int32_t cap_wide;        // most CTAs of the peeling (and TensorHypE) group; 0 = no cap
     int32_t cap_narrow;      // most CTAs of the sort / statistics / CSR / niching / survivor groups; 0 = no cap
-    int32_t pad_shape_;
+    int32_t ranked;          // MODE_SELECT from the given ranks rank_in (no dominance matrix, no peeling)
+    const int32_t* rank_in;  // [n2] caller-order ranks (EMO_NOT_RANKED beyond the last needed front)
 };
 
 // Per-problem scalars; zeroed by the prep kernel.
@@ -100,7 +101,7 @@ struct Scal {
     int32_t ncol;            // niching: keys collected from the selected histogram bin
     int32_t nsel;            // one-shot niching: references that took their nearest candidate
     int32_t longrun;         // sort: a run of equal f_1 longer than the in-place fix-up handles
-    int32_t pad2_;
+    int32_t lfinal1;         // wavefront peeling: l + 1 once known, 0 before
 };
 
 // Device-side descriptor with every workspace pointer of one problem.
@@ -118,8 +119,13 @@ struct ProbDev {
     int32_t* cnt;            // [n2p] dominator counts (sorted order)
     int32_t* rank_s;         // [n2p] ranks (sorted order)
     int32_t* rank_o;         // [n2]  ranks (caller order)
-    int32_t* front;          // [3][n2p] front members grouped by column block (3 buffers)
+    int32_t* front;          // [3][n2p] front members grouped by column block (3 buffers); the
+                             // wavefront peeling keeps each block's members in front order in the first
     int32_t* front_n;        // [3][ncb] members per column block
+    int32_t* wdone;          // [ncb] wavefront: fronts whose counts block cb has applied (INT32_MAX: exhausted)
+    int32_t* wmaxf;          // [ncb] wavefront: last front with offsets of an exhausted block
+    int32_t* wcnt;           // [n2 + 2] wavefront: members of front k
+    uint16_t* wofs;          // [ncb][n2 + 2] wavefront: start of front k in block cb's member list
     int32_t* slist;          // [n2] caller indices of S = {rank <= l}
     int32_t* pi;             // [n2] associated reference
     double* d64;             // [n2] perpendicular distance (FP64)
@@ -230,6 +236,9 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
     int64_t o_rank_o = take(n2 * 4);
     int64_t o_front = take(3 * n2p * 4);
     int64_t o_front_n = take(3 * ncb * 4);
+    int64_t o_wdone = take(2 * ncb * 4);
+    int64_t o_wcnt = take((n2 + 2) * 4);
+    int64_t o_wofs = in.ranked ? 0 : take(ncb * (n2 + 2) * 2);
     int64_t o_slist = take(n2 * 4);
     int64_t o_hist = take(int64_t(G) * kRadix * 4);
     int64_t o_flag = take((n2p + 1) * 4);
@@ -263,8 +272,10 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         o_llist = take(2 * n2 * 4);
         o_ekeys = take((n2 + 1) * 8);
     }
-    int64_t o_colpre = take(ncb * (m - 1) * colprep_obj_bytes((int)(m - 1)));
-    int64_t o_D = take(ntiles * 4096);
+    // the prefix sets, the dominance tiles and the wavefront offsets are not
+    // needed when the ranks are given
+    int64_t o_colpre = in.ranked ? 0 : take(ncb * (m - 1) * colprep_obj_bytes((int)(m - 1)));
+    int64_t o_D = in.ranked ? 0 : take(ntiles * 4096);
     if (base && d) {
         d->in = in;
         d->nrb = (int32_t)nrb;
@@ -281,6 +292,10 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         d->rank_o = (int32_t*)(base + o_rank_o);
         d->front = (int32_t*)(base + o_front);
         d->front_n = (int32_t*)(base + o_front_n);
+        d->wdone = (int32_t*)(base + o_wdone);
+        d->wmaxf = d->wdone + ncb;
+        d->wcnt = (int32_t*)(base + o_wcnt);
+        d->wofs = in.ranked ? nullptr : (uint16_t*)(base + o_wofs);
         d->slist = (int32_t*)(base + o_slist);
         d->hist = (int32_t*)(base + o_hist);
         d->flag = (int32_t*)(base + o_flag);
@@ -301,8 +316,8 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         d->rphi2 = in.mode == MODE_SELECT ? (float*)(base + o_rphi2) : nullptr;
         d->rsort = in.mode == MODE_SELECT ? (float*)(base + o_rsort) : nullptr;
         d->flagged_bound = in.mode == MODE_SELECT ? (float*)(base + o_fbound) : nullptr;
-        d->colpre = (unsigned char*)(base + o_colpre);
-        d->D = (uint32_t*)(base + o_D);
+        d->colpre = in.ranked ? nullptr : (unsigned char*)(base + o_colpre);
+        d->D = in.ranked ? nullptr : (uint32_t*)(base + o_D);
     }
     return off;
 }

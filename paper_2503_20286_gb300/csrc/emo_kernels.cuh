@@ -191,12 +191,19 @@ __host__ __device__ constexpr int peel_smem_bytes(int ncb)
 {
     return kPeelRingBytes + (ncb + 1 + kPeelChunk) * (int)sizeof(int);
 }
+__global__ void k_peel_wave(Plan* plan);
+__global__ void k_rank_in(Plan* plan);
+cudaError_t launch_front_counts(const uint32_t* D, int64_t ld, int64_t ncols, const int32_t* rows, int64_t n_rows,
+                                int32_t* counts, uint8_t* new_front, int sms, cudaStream_t s);
+__host__ __device__ constexpr int peel_wave_smem_bytes(int ncb) { return peel_smem_bytes(ncb) + 2 * ncb * (int)sizeof(int); }
 __global__ void k_stats(Plan* plan);
 __global__ void k_rescan(Plan* plan);
 __global__ void k_csr(Plan* plan);
 __global__ void k_niche(Plan* plan);
 __global__ void k_niche_oneshot(Plan* plan);
-__global__ void k_hype(Plan* plan);
+__global__ void k_hype(Plan* plan, int phase);
+__global__ void k_hype_counts(Plan* plan);
+int hype_counts_smem(int m);
 __global__ void k_finish(Plan* plan);
 
 // Dominance kernels, one instantiation per objective count (k_dominance.cu).
@@ -205,7 +212,7 @@ cudaError_t launch_dominance_tri_range(int m, Plan* plan, int sms, cudaStream_t 
                                        unsigned long long* counter, int pfirst, int plast);
 cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, cudaStream_t s);
 cudaError_t launch_colprep(Plan* plan, int sms, cudaStream_t s, int nprob);
-cudaError_t launch_dominance_full_c(const float* F, int64_t n2, int m, uint32_t* D, int64_t ld, int32_t* cnt,
-                                    int sms, cudaStream_t s);
+cudaError_t launch_dominance_full_c(const float* F, int64_t n2, int64_t col_lo, int64_t col_hi, int m, uint32_t* D,
+                                    int64_t ld, int32_t* cnt, int sms, cudaStream_t s);
 
 }  // namespace emo

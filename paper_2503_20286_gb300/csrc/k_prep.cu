@@ -94,6 +94,7 @@ __global__ void k_prep(Plan* plan)
     }
     for (int64_t i = tid; i < n2; i += stride) d.rank_o[i] = kNotRanked;
     for (int64_t c = tid; c < 3 * (int64_t)d.ncb; c += stride) d.front_n[c] = 0;
+    for (int64_t c = tid; c < n2 + 2; c += stride) d.wcnt[c] = 0;  // front sizes of the wavefront peeling
     for (int64_t c = tid; c < d.ncb; c += stride) d.minrs[c] = INT32_MAX;
     if (in.mode == MODE_SELECT) {
         for (int64_t j = tid; j < in.n_r; j += stride) {

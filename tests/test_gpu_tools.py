@@ -26,7 +26,7 @@ def test_autotune_writes_and_reuses_the_cache_and_keeps_results(tmp_path):
     emo.emo_autotune(3, 20000, path)
     lines = open(path).read().split()
     major, minor = torch.cuda.get_device_capability()
-    assert len(lines) == 7 and lines[0] == str(10 * major + minor) and lines[1:3] == ["3", "14"]
+    assert len(lines) == 8 and lines[0] == str(10 * major + minor) and lines[1:3] == ["3", "14"]
     assert int(lines[3]) in (2, 4, 8, 16, 32)
     assert int(lines[4]) in (64, 128, 256, 512, 1024)
     G = default["peel_ctas"]
@@ -34,6 +34,7 @@ def test_autotune_writes_and_reuses_the_cache_and_keeps_results(tmp_path):
     shape = emo.emo_launch_shape(3, 20000)
     assert shape["assoc_blocks_per_sm"] == int(lines[3]) and shape["dom_rowblocks_per_item"] == int(lines[4])
     assert shape["other_coop_ctas"] <= shape["peel_ctas"] <= G
+    assert shape["peel_wavefront"] == int(lines[7]) in (0, 1)
     emo.emo_autotune(3, 20000, path)               # found in the cache: nothing appended
     assert open(path).read().split() == lines
     p = wl.config(1)                                # 2N = 20,000, M = 3: runs with the tuned shapes
