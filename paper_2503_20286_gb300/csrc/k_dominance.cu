@@ -544,9 +544,12 @@ struct FullSmem {
     long long item;
 };
 
+// Columns [col_lo, col_hi) (col_lo a multiple of 1024); D word w of a row
+// holds columns col_lo + 32 w .. + 31, dom_count[j - col_lo] their sums.
 template <int M>
-__global__ void __launch_bounds__(256, 1) k_dom_full(const float* __restrict__ F, int64_t n2, uint32_t* D,
-                                                     int64_t ld, int32_t* cnt, long long nitems)
+__global__ void __launch_bounds__(256, 1) k_dom_full(const float* __restrict__ F, int64_t n2, int64_t col_lo,
+                                                     int64_t col_hi, uint32_t* D, int64_t ld, int32_t* cnt,
+                                                     long long nitems)
 {
     constexpr int R = 2, NW = 8;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -554,12 +557,13 @@ __global__ void __launch_bounds__(256, 1) k_dom_full(const float* __restrict__ F
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nrb = (int)cdiv(n2, 32);
     const long long per_cb = cdiv(nrb, kDomRowChunk);
+    const int cb_lo = (int)(col_lo / kColBlock);
     for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int cb = (int)(item / per_cb), chunk = (int)(item % per_cb);
+        const int cb = cb_lo + (int)(item / per_cb), chunk = (int)(item % per_cb);
         const int64_t cbase = (int64_t)cb * kColBlock;
         for (int i = tid; i < kColBlock * M; i += blockDim.x) {
             const int64_t q = cbase + i / M;
-            sm.ck[i] = q < n2 ? F[q * M + i % M] + 0.0f : -INFINITY;
+            sm.ck[i] = q < col_hi ? F[q * M + i % M] + 0.0f : -INFINITY;
         }
         for (int i = tid; i < kColBlock; i += blockDim.x) sm.cnt[i] = 0;
         __syncthreads();
@@ -607,7 +611,7 @@ __global__ void __launch_bounds__(256, 1) k_dom_full(const float* __restrict__ F
                 for (int row = 0; row < 32; ++row) x[row] = sm.tiles[warp][r][row * 32 + (lane ^ row)];
                 vc.add16(x);
                 vc.add16(x + 16);
-                const int64_t wcol = (int64_t)cb * 32 + lane;
+                const int64_t wcol = (int64_t)(cb - cb_lo) * 32 + lane;
                 if (wcol < ld) {
 #pragma unroll 4
                     for (int row = 0; row < 32; ++row) {
@@ -629,7 +633,7 @@ __global__ void __launch_bounds__(256, 1) k_dom_full(const float* __restrict__ F
             __syncthreads();
             for (int q = tid; q < kColBlock; q += blockDim.x) {
                 const int c = sm.cnt[(q & 31) * 32 + (q >> 5)];
-                if (c && cbase + q < n2) atomicAdd(&cnt[cbase + q], c);
+                if (c && cbase + q < col_hi) atomicAdd(&cnt[cbase + q - col_lo], c);
             }
         }
         __syncthreads();
@@ -672,8 +676,8 @@ static cudaError_t launch_tri_rt(int K, Plan* plan, int sms, cudaStream_t s, lon
 }
 
 template <int M>
-static cudaError_t launch_full_m(const float* F, int64_t n2, uint32_t* D, int64_t ld, int32_t* cnt, int sms,
-                                 cudaStream_t s)
+static cudaError_t launch_full_m(const float* F, int64_t n2, int64_t col_lo, int64_t col_hi, uint32_t* D, int64_t ld,
+                                 int32_t* cnt, int sms, cudaStream_t s)
 {
     const size_t smem = sizeof(FullSmem<M>);
     cudaError_t e = cudaFuncSetAttribute(k_dom_full<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -681,10 +685,10 @@ static cudaError_t launch_full_m(const float* F, int64_t n2, uint32_t* D, int64_
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dom_full<M>, 256, smem);
     if (e != cudaSuccess) return e;
-    const long long nitems = cdiv(n2, kColBlock) * cdiv(cdiv(n2, 32), kDomRowChunk);
+    const long long nitems = cdiv(col_hi - col_lo, kColBlock) * cdiv(cdiv(n2, 32), kDomRowChunk);
     long long grid = (long long)sms * (occ > 0 ? occ : 1);
     if (grid > nitems) grid = nitems;
-    k_dom_full<M><<<(unsigned)grid, 256, smem, s>>>(F, n2, D, ld, cnt, nitems);
+    k_dom_full<M><<<(unsigned)grid, 256, smem, s>>>(F, n2, col_lo, col_hi, D, ld, cnt, nitems);
     return cudaGetLastError();
 }
 
@@ -715,12 +719,12 @@ cudaError_t launch_dominance_tri_range(int m, Plan* plan, int sms, cudaStream_t 
     }
 }
 
-cudaError_t launch_dominance_full_c(const float* F, int64_t n2, int m, uint32_t* D, int64_t ld, int32_t* cnt,
-                                    int sms, cudaStream_t s)
+cudaError_t launch_dominance_full_c(const float* F, int64_t n2, int64_t col_lo, int64_t col_hi, int m, uint32_t* D,
+                                    int64_t ld, int32_t* cnt, int sms, cudaStream_t s)
 {
     switch (m) {
 #define X(MM) \
-    case MM: return launch_full_m<MM>(F, n2, D, ld, cnt, sms, s);
+    case MM: return launch_full_m<MM>(F, n2, col_lo, col_hi, D, ld, cnt, sms, s);
         EMO_FOR_EACH_M(X)
 #undef X
     default: return cudaErrorInvalidValue;

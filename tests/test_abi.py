@@ -70,6 +70,13 @@ def test_host_argument_checks_reject_before_launch(lib):
     assert L.emo_autotune(1, 1000, None) == 1                                                        # m < 2
     assert L.emo_launch_shape(3, 1000, None) == 1                                                    # no output
     assert L.emo_launch_shape(17, 1000, p) == 1                                                      # m > 16
+    assert L.emo_dominance_cols(p, 3000, 3, 1000, 2000, p, 40, None, None) == 1        # col_lo not a block start
+    assert L.emo_dominance_cols(p, 3000, 3, 1024, 3001, p, 40, None, None) == 1        # col_hi > n2
+    assert L.emo_dominance_cols(p, 3000, 3, 1024, 2048, p, 31, None, None) == 1        # ld < 32 words
+    assert L.emo_front_counts(p, 4, 100, None, 5, p, p, None) == 1                     # rows missing
+    assert L.emo_front_counts(p, 3, 100, p, 5, p, p, None) == 1                        # ld < 4 words
+    assert L.emo_nsga3_select_ranked(p, 10, 3, p, 5, 5, 0, 0, None, p, None, p, 1 << 20, None) == 1  # no ranks
+    assert L.emo_workspace_size(6, 1000, 3, 0) == 0                                    # ranked: no directions
     assert L.emo_get_last_device_status(None, None) == 1
     assert L.emo_hype_select(p, 10, 3, p, p, 0, 5, p, None, None, p, 1 << 20, None) == 1           # s = 0
     assert L.emo_workspace_size(2, 0, 3, 5) == 0
