@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-population batched-vs-plain timing")
     ap.add_argument("--no-parity", action="store_true",
                     help="skip the per-workload oracle timing and error report of the CPU-baseline leg")
+    ap.add_argument("--profile-op", choices=["select", "rank", "dominance", "hype", "moead", "generation"],
+                    help="profiling mode: run --profile-calls calls of one operation on the sphere-front "
+                         "stand-in of --n2 points (M = --profile-m) and print its stage times; nothing else runs")
+    ap.add_argument("--profile-m", type=int, default=M)
+    ap.add_argument("--profile-calls", type=int, default=2)
     return ap.parse_args()
 
 
@@ -697,10 +702,68 @@ def run_reference(args):
     return 0
 
 
+def profile_mode(args):
+    """A few calls of one operation, for a profiler attached to this process:
+    only the inputs, outputs and workspace are allocated, so that replays
+    stay small; prints the stage times of the last call."""
+    import torch
+    from paper_2503_20286_gb300 import _binding as emo
+    from paper_2503_20286_gb300 import build as emo_build
+    from paper_2503_20286_gb300 import workloads as wl
+    emo_build.build()
+    dev = torch.device("cuda")
+    n2, m, op = args.n2, args.profile_m, args.profile_op
+    F = wl.population(n2, m, m + 9, "sphere", wl.BASE_SEED + 4)
+    R = wl.das_dennis(H if (n2 == N2 and m == M) else wl.h_for_count(n2 // 2, m), m)
+    Ft, Rt = torch.from_numpy(F).to(dev), torch.from_numpy(R).to(dev)
+    emo.emo_set_stage_timing(True)
+    out = {}
+    if op == "select":
+        ws = torch.empty(emo.emo_workspace_size(emo.EMO_OP_NSGA3_SELECT, n2, m, R.shape[0]), dtype=torch.uint8,
+                         device=dev)
+        surv = torch.empty(n2 // 2, dtype=torch.int32, device=dev)
+        for c in range(args.profile_calls):
+            emo.emo_nsga3_select(Ft, Rt, n2 // 2, 1, c, survivors=surv, ws=ws)
+    elif op == "rank":
+        ws = torch.empty(emo.emo_workspace_size(emo.EMO_OP_ND_RANK, n2, m, 0), dtype=torch.uint8, device=dev)
+        for c in range(args.profile_calls):
+            emo.emo_nd_rank(Ft, 0, ws=ws)
+    elif op == "dominance":
+        D = torch.empty((n2, (n2 + 31) // 32), dtype=torch.int32, device=dev)
+        for c in range(args.profile_calls):
+            emo.emo_dominance(Ft, D=D)
+    elif op == "hype":
+        U = np.random.Generator(np.random.Philox(7)).random((10_000, m)).astype(np.float32)
+        v_ref = (F.max(axis=0) * np.float32(1.1)).astype(np.float32)
+        Ut, vt = torch.from_numpy(U).to(dev), torch.from_numpy(v_ref).to(dev)
+        ws = torch.empty(emo.emo_workspace_size(emo.EMO_OP_HYPE_SELECT, n2, m, 10_000), dtype=torch.uint8, device=dev)
+        for c in range(args.profile_calls):
+            emo.emo_hype_select(Ft, vt, Ut, n2 // 2, ws=ws)
+    elif op == "moead":
+        X, F1, O, F2, z, W, I_nb = moead_inputs(wl.h_for_count(n2 // 2, m), m, m + 9, 20, seed=0x250320286)
+        T = {k: torch.from_numpy(v).to(dev) for k, v in dict(X=X, F1=F1, O=O, F2=F2, z=z, W=W, I=I_nb).items()}
+        for c in range(args.profile_calls):
+            emo.emo_moead_select(T["X"], T["F1"], T["O"], T["F2"], T["z"].clone(), T["W"], T["I"], 5.0)
+        out["subproblems"] = int(W.shape[0])
+    else:
+        X = torch.from_numpy(wl.decision_vectors(n2 // 2, m + 9, wl.BASE_SEED + 4, stream=5)).to(dev)
+        Fg = emo.emo_standin_objectives(X, m, emo.EMO_SHAPE_SPHERE)
+        for c in range(args.profile_calls):
+            emo.emo_nsga3_generation(X, Fg, Rt, emo.EMO_SHAPE_SPHERE, wl.BASE_SEED + 4, c)
+    torch.cuda.synchronize()
+    emo.emo_set_stage_timing(False)
+    out.update({"profile_op": op, "n2": n2, "m": m, "n_r": int(R.shape[0]), "calls": args.profile_calls,
+                "stage_ms": dict(emo.emo_stage_times()) if op not in ("dominance", "moead") else {}})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_op:
+        return profile_mode(args)
 
     import torch
     import torch.distributed as dist
