@@ -242,6 +242,178 @@ __device__ __forceinline__ unsigned long long niche_key(uint64_t seed, uint64_t 
     return ((unsigned long long)niche_random(seed, gen, (uint32_t)j, (uint32_t)c, 0u) << 32) | (unsigned)j;
 }
 
+constexpr int kNicheDirectLevels = 3;  // levels served one at a time before the bulk form
+
+// Pick of reference j at level c (the level form's step): its nearest
+// candidate at level 0 (the list is untouched then), else the candidate of
+// rank (u |C_j|) >> 32 among the remaining ones (Fenwick tree over the list).
+__device__ __forceinline__ void niche_pick(const ProbDev& d, const int32_t* L, uint64_t seed, uint64_t gen, int64_t j,
+                                           int c, int len)
+{
+    const int off = d.loff[j], full = d.loff[j + 1] - off;
+    int pos;
+    if (c == 0) {
+        pos = niche_nearest(d, L, off, full);
+    } else {
+        const uint32_t u = niche_random(seed, gen, (uint32_t)j, (uint32_t)c, 1u);
+        const int rank = (int)(((unsigned long long)u * (unsigned long long)len) >> 32);
+        pos = fen_select(d.fen + off, full, rank);
+    }
+    d.flag[L[off + pos]] = 1;
+    fen_remove(d.fen + off, full, pos);
+}
+
+// The remaining picks in bulk (water-filling). From the current niche counts
+// rho_j and live list lengths n_j, the level form serves reference j at the
+// levels c = rho_j .. rho_j + n_j - 1 (one member per level while its list
+// lasts). With ne(c) = #{j : rho_j <= c < rho_j + n_j} references at level c
+// and P(c) = sum_{c' < c} ne(c') picks before it, the level form stops at the
+// smallest c* with P(c*) + ne(c*) >= remaining and there serves only the
+// remaining - P(c*) references of smallest priority. Each reference then
+// makes its picks itself, in level order, with the level form's draws, so the
+// picks are the same. `handled` is false (nothing done) when the levels span
+// more than kNicheBins values; the caller then goes on level by level.
+__device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, int remaining, NicheSmem& sm,
+                           const int32_t* L, int& levels, bool& handled)
+{
+    Scal* sc = d.sc;
+    const ProbIn& in = d.in;
+    const int tid = threadIdx.x;
+    const int nr = in.n_r;
+    const uint64_t seed = in.seed, gen = in.gen;
+    const int64_t t0 = (int64_t)g.rank * blockDim.x + tid;
+    const int64_t stride = (int64_t)g.size * blockDim.x;
+    int32_t* hist = d.nhist;
+    unsigned long long* part = reinterpret_cast<unsigned long long*>(d.nhist + kNicheBins);
+    __shared__ int s_cstar, s_pstar, s_nestar, s_lev;
+    handled = false;
+
+    // (1) the span of levels [c_lo, c_end) of the live references
+    int cmin = INT32_MAX, cend = 0;
+    for (int64_t j = t0; j < nr; j += stride) {
+        const int n = __ldcg(&d.lcnt[j]);
+        if (n > 0) {
+            const int r = __ldcg(&d.rho[j]);
+            cmin = min(cmin, r);
+            cend = max(cend, r + n);
+        }
+    }
+    const int bmin = block_reduce_min<kCoopThreads>(cmin, sm.warp);
+    const int bend = -block_reduce_min<kCoopThreads>(-cend, sm.warp);
+    if (tid == 0) part[g.rank] = ((unsigned long long)(unsigned)bmin << 32) | (unsigned)bend;
+    for (int64_t b = t0; b < kNicheBins; b += stride) hist[b] = 0;
+    if (!group_sync(sc, g.size, budget)) return false;
+    int lm = INT32_MAX, le = 0;
+    for (int r = tid; r < g.size; r += blockDim.x) {
+        const unsigned long long v = __ldcg(&part[r]);
+        lm = min(lm, (int)(v >> 32));
+        le = max(le, (int)(v & 0xFFFFFFFFull));
+    }
+    const int c_lo = block_reduce_min<kCoopThreads>(lm, sm.warp);
+    const int c_end = -block_reduce_min<kCoopThreads>(-le, sm.warp);
+    if (c_lo == INT32_MAX) {  // no live reference although picks remain
+        if (g.rank == 0 && tid == 0) set_status(sc, EMO_ERR_INVALID_ARG);
+        return false;
+    }
+    const int R = c_end - c_lo;
+    if (R > kNicheBins) return true;  // too wide for the histogram: level by level
+
+    // (2) ne(c) as a difference array over the span
+    for (int64_t j = t0; j < nr; j += stride) {
+        const int n = __ldcg(&d.lcnt[j]);
+        if (n > 0) {
+            const int r = __ldcg(&d.rho[j]) - c_lo;
+            atomicAdd(&hist[r], 1);
+            if (r + n < R) atomicAdd(&hist[r + n], -1);
+        }
+    }
+    if (!group_sync(sc, g.size, budget)) return false;
+
+    // (3) every CTA: ne(c), P(c), c*, and the levels served up to c*
+    {
+        constexpr int PER = kNicheBins / kCoopThreads;
+        int dv[PER], run = 0;
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int c = tid * PER + e;
+            dv[e] = c < R ? __ldcg(&hist[c]) : 0;
+            run += dv[e];
+        }
+        int tot;
+        int pre = block_exclusive_scan<kCoopThreads>(run, sm.warp, tot);  // ne at this thread's first level
+        int ne[PER], nsum = 0;
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            pre += dv[e];
+            ne[e] = pre;
+            nsum += pre;
+        }
+        int ppre = block_exclusive_scan<kCoopThreads>(nsum, sm.warp, tot);  // P at this thread's first level
+        if (tid == 0) s_cstar = INT32_MAX;
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int c = tid * PER + e;
+            if (c < R && ne[e] > 0 && ppre + ne[e] >= remaining) atomicMin(&s_cstar, c);
+            ppre += ne[e];
+        }
+        __syncthreads();
+        const int cs = s_cstar;
+        int lev = 0;
+        ppre -= nsum;
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int c = tid * PER + e;
+            if (c == cs) {
+                s_pstar = ppre;
+                s_nestar = ne[e];
+            }
+            if (c <= cs && c < R && ne[e] > 0) ++lev;
+            ppre += ne[e];
+        }
+        lev = block_reduce_sum<kCoopThreads>(lev, sm.warp);
+        if (tid == 0) s_lev = lev;
+        __syncthreads();
+    }
+    const int cstar = s_cstar;
+    if (cstar == INT32_MAX) {  // fewer live candidates than picks: inconsistent lists
+        if (g.rank == 0 && tid == 0) set_status(sc, EMO_ERR_INVALID_ARG);
+        return false;
+    }
+    const int c_star = c_lo + cstar, rem = remaining - s_pstar, ne_star = s_nestar;
+    const bool all = ne_star <= rem;
+    unsigned long long thresh = ~0ull;
+    if (!all) {  // the rem references of smallest priority among those at level c*
+        if (!group_sync(sc, g.size, budget)) return false;  // every CTA is done with the histogram
+        for (int64_t b = t0; b < kNicheBins; b += stride) hist[b] = 0;
+        if (g.rank == 0 && tid == 0) sc->ncol = 0;
+        if (!group_sync(sc, g.size, budget)) return false;
+        auto level_keys = [&](auto&& f) {
+            for (int64_t j = t0; j < nr; j += stride) {
+                const int n = __ldcg(&d.lcnt[j]), r = __ldcg(&d.rho[j]);
+                if (n > 0 && r <= c_star && c_star < r + n) f(niche_key(seed, gen, j, c_star));
+            }
+        };
+        if (!group_kth_key(d, g, budget, rem - 1, level_keys, sm, thresh)) return false;
+    }
+
+    // (4) the picks of every reference, in level order
+    for (int64_t j = t0; j < nr; j += stride) {
+        const int n = d.lcnt[j];
+        if (n <= 0) continue;
+        const int r = d.rho[j];
+        int take = r < c_star ? min(c_star, r + n) - r : 0;
+        if (r <= c_star && c_star < r + n && (all || niche_key(seed, gen, j, c_star) <= thresh)) ++take;
+        for (int t = 0; t < take; ++t) niche_pick(d, L, seed, gen, j, r + t, n - t);
+        d.lcnt[j] = n - take;
+        d.rho[j] = r + take;
+    }
+    if (!group_sync(sc, g.size, budget)) return false;
+    levels += s_lev;
+    handled = true;
+    return true;
+}
+
 __global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
 {
     __shared__ NicheSmem sm;
@@ -336,6 +508,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
         if (!group_sync(sc, g.size, budget)) return;
         remaining -= all ? ne : remaining;
         ++levels;
+        if (remaining > 0 && levels >= kNicheDirectLevels) {  // the rest in bulk when the span allows
+            bool handled = false;
+            if (!niche_bulk(d, g, budget, remaining, sm, L, levels, handled)) return;
+            if (handled) remaining = 0;
+        }
     }
     if (g.rank == 0 && tid == 0) sc->levels = levels;
 }

@@ -45,6 +45,10 @@ def compare_select(F, R, n_keep, seed, gen=0, check_debug=True, mode=0):
     assert info["status"] == 0, info
     assert info["last_rank"] == t["last_rank"]
     assert info["n_before"] == t["n_before"] and info["n_last"] == t["n_last"]
+    if mode == 0 and t["n_last"] > n_keep - t["n_before"]:
+        # niching levels of Algorithm S.1 (served one at a time or in bulk); when
+        # the whole last front survives no level is run on the device
+        assert info["n_levels"] == t["n_levels"], (info["n_levels"], t["n_levels"])
     if check_debug:
         l = t["last_rank"]
         S = t["rank"] <= l

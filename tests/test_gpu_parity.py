@@ -241,3 +241,15 @@ def test_bounded_wait_times_out_and_context_survives():
     finally:
         emo.emo_set_spin_budget(0)
     _gpu.compare_select(F, R, 2500, seed=1)
+
+
+@pytest.mark.parametrize("n2,m,h,keep_frac,q", [(6000, 3, 3, 0.5, None), (12000, 5, 2, 0.6, 8.0),
+                                                (4000, 8, 1, 0.45, 16.0), (20000, 3, 6, 0.9, None)])
+def test_many_niching_levels(n2, m, h, keep_frac, q):
+    """Few reference directions and a large last front: hundreds of niching
+    levels, served one at a time and then in bulk (the same picks and level
+    count as the oracle's loop of Algorithm S.1)."""
+    F = wl.population(n2, m, m + 5, "sphere", seed=800 + n2 + m, quantize=q)
+    R = wl.das_dennis(h, m)
+    info, t = _gpu.compare_select(F, R, int(keep_frac * n2), seed=3, gen=5)
+    assert t["n_levels"] > 20
