@@ -40,7 +40,7 @@ KERNELS_PER_STEP = 12                     # launches of one single-population se
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n2", type=int, default=N2, help="population size (default: the 400k workload)")
@@ -90,7 +90,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -432,6 +432,48 @@ def generation_loop(emo, torch, dev, flush, stream, gens: int = 20, n: int = N2 
             "igd_front": f"Das-Dennis H={H} directions projected onto the unit sphere",
             "last_info": dict(zip(("status", "last_rank", "n_before", "n_last", "fallback_used", "n_recheck",
                                    "n_fronts", "n_levels"), info.cpu().tolist()))}
+
+
+def dominance_call_timing(emo, torch, dev, flush, stream, steps):
+    """emo_dominance (the first call of the boundary: the full matrix in the
+    caller's order) at 2N = 100,000 and 400,000, M = 3: the direct
+    pair-by-pair kernel and the prefix-set form (emo_dominance_ws). Bytes:
+    the (2N)^2 / 8 written; device time per call (CUDA events, L2 flushed
+    before each); both must give the same matrix."""
+    from paper_2503_20286_gb300 import workloads as wl
+    out = {}
+    pk = peaks()
+    for n2 in (100_000, N2):
+        F = torch.from_numpy(wl.population(n2, M, D_VARS, "sphere", wl.BASE_SEED + 4)).to(dev)
+        ld = (n2 + 31) // 32
+        D = torch.empty((n2, ld), dtype=torch.int32, device=dev)
+        c = torch.empty(n2, dtype=torch.int32, device=dev)
+        ws = torch.empty(max(1, emo.emo_workspace_size(emo.EMO_OP_DOMINANCE_WS, n2, M, 0)), dtype=torch.uint8,
+                         device=dev)
+        res = {}
+        for name, call in (("prefix_sets", lambda: emo.emo_dominance_ws(F, D=D, dom_count=c, ws=ws, stream=stream)),
+                           ("direct", lambda: emo.emo_dominance(F, D=D, dom_count=c, stream=stream))):
+            call()
+            ms = []
+            for _ in range(steps if (name == "prefix_sets" or n2 < N2) else 1):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                call()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            t = statistics.median(ms)
+            byt = n2 * ld * 4
+            res[name] = {"ms": t, "GBps": byt / (t / 1e3) / 1e9, "frac_of_hbm": byt / (t / 1e3) / 1e9 / pk["hbm_gbs"]}
+            if name == "prefix_sets":
+                ref = (D.clone(), c.clone())
+        res["identical"] = bool(torch.equal(ref[0], D) and torch.equal(ref[1], c))
+        res["matrix_bytes"] = n2 * ld * 4
+        out[f"n2_{n2}"] = res
+        del D, ws, ref
+        torch.cuda.empty_cache()
+    return out
 
 
 def batched_sharded(emo, torch, dev, world: int, rank: int, rounds: int = 5):
@@ -903,6 +945,10 @@ def main():
             line["moead"] = moead_timing(emo, torch, dev, flush, stream, max(3, args.steps // 2))
         except Exception as e:  # reported in the line; the selection numbers above stand
             line["moead"] = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            line["emo_dominance"] = dominance_call_timing(emo, torch, dev, flush, stream, max(3, args.steps // 2))
+        except Exception as e:  # reported in the line; the selection numbers above stand
+            line["emo_dominance"] = {"error": f"{type(e).__name__}: {e}"}
         try:
             line["generation_loop"] = generation_loop(emo, torch, dev, flush, stream)
         except Exception as e:  # reported in the line; the selection numbers above stand

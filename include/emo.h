@@ -60,7 +60,7 @@ typedef struct {
     int32_t fallback_used; /* 1: nadir point replaced the intercepts        */
     int32_t n_recheck;     /* points associated by an all-reference FP64 scan */
     int32_t n_fronts;      /* fronts peeled (l + 1 for selection)           */
-    int32_t n_levels;      /* niching levels run                            */
+    int32_t n_levels;      /* niching levels run (0: all of front l kept)   */
 } emo_select_info;
 
 /* Optional intermediate outputs of emo_nsga3_select_debug (device pointers,
@@ -100,7 +100,8 @@ typedef enum {
     EMO_OP_HYPE_SELECT = 3,
     EMO_OP_MOEAD_SELECT = 4, /* emo_workspace_size(EMO_OP_MOEAD_SELECT, n, m, T) */
     EMO_OP_IGD = 5,          /* emo_workspace_size(EMO_OP_IGD, n_ref, m, 0) */
-    EMO_OP_SELECT_RANKED = 6 /* emo_nsga3_select_ranked (no dominance matrix) */
+    EMO_OP_SELECT_RANKED = 6, /* emo_nsga3_select_ranked (no dominance matrix) */
+    EMO_OP_DOMINANCE_WS = 7   /* emo_dominance_ws (0 for m > 5: no workspace needed) */
 } emo_op;
 
 /* Front shapes of the stand-in objective functions (emo_standin_objectives). */
@@ -125,6 +126,21 @@ size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r);
  */
 emo_status emo_dominance(const float* F, int64_t n2, int32_t m, uint32_t* D, int64_t ld_words,
                          int32_t* dom_count, emo_stream_t stream);
+
+/*
+ * The same matrix and counts as emo_dominance, computed through sorted
+ * per-objective prefix sets of 1024-column blocks of the caller's order
+ * instead of pair-by-pair compares: q is dominated by p iff it lies in every
+ * objective's prefix {q : f_k(q) >= f_k(p)} and is not identical to p
+ * (identical points are the runs of a lexicographic sort). For m <= 5; for
+ * larger m it runs the direct kernel of emo_dominance (ws unused). ws:
+ * emo_workspace_size(EMO_OP_DOMINANCE_WS, n2, m, 0) bytes, 256-byte aligned
+ * (about 0.2 x n2 x m KB: the prefix sets). Non-finite objectives give
+ * EMO_ERR_NONFINITE in the workspace status word (the matrix is then
+ * undefined).
+ */
+emo_status emo_dominance_ws(const float* F, int64_t n2, int32_t m, uint32_t* D, int64_t ld_words, int32_t* dom_count,
+                            void* ws, size_t ws_bytes, emo_stream_t stream);
 
 /*
  * emo_dominance restricted to the columns [col_lo, col_hi) (col_lo a multiple

@@ -20,7 +20,7 @@ EMO_OK = 0
 STATUS_NAMES = {0: "EMO_OK", 1: "EMO_ERR_INVALID_ARG", 2: "EMO_ERR_NONFINITE", 3: "EMO_ERR_WORKSPACE",
                 4: "EMO_ERR_CUDA", 5: "EMO_ERR_TIMEOUT", 6: "EMO_ERR_NOT_IMPLEMENTED"}
 EMO_OP_DOMINANCE, EMO_OP_ND_RANK, EMO_OP_NSGA3_SELECT, EMO_OP_HYPE_SELECT, EMO_OP_MOEAD_SELECT, EMO_OP_IGD, \
-    EMO_OP_SELECT_RANKED = range(7)
+    EMO_OP_SELECT_RANKED, EMO_OP_DOMINANCE_WS = range(8)
 EMO_SHAPE_LINEAR, EMO_SHAPE_SPHERE = 0, 1
 EMO_NOT_RANKED = 2147483647
 EMO_NICHE_EXACT, EMO_NICHE_ONESHOT = 0, 1
@@ -80,6 +80,8 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             L.emo_workspace_size.argtypes = [ctypes.c_int, i64, i32, i32]
             L.emo_dominance.restype = ctypes.c_int
             L.emo_dominance.argtypes = [vp, i64, i32, vp, i64, vp, vp]
+            L.emo_dominance_ws.restype = ctypes.c_int
+            L.emo_dominance_ws.argtypes = [vp, i64, i32, vp, i64, vp, vp, sz, vp]
             L.emo_dominance_cols.restype = ctypes.c_int
             L.emo_dominance_cols.argtypes = [vp, i64, i32, i64, i64, vp, i64, vp, vp]
             L.emo_front_counts.restype = ctypes.c_int
@@ -188,6 +190,25 @@ def emo_dominance(F: torch.Tensor, D: torch.Tensor | None = None, dom_count: tor
         dom_count = torch.empty(n2, dtype=torch.int32, device=F.device)
     _check(lib().emo_dominance(_ptr(F), n2, m, _ptr(D), D.shape[1], _ptr(dom_count), _stream(stream)),
            "emo_dominance")
+    return D, dom_count
+
+
+def emo_dominance_ws(F: torch.Tensor, D: torch.Tensor | None = None, dom_count: torch.Tensor | None = None,
+                     ws: torch.Tensor | None = None, stream=None):
+    """emo_dominance through sorted prefix sets (m <= 5; a workspace)."""
+    n2, m = F.shape
+    ld = (n2 + 31) // 32
+    if D is None:
+        D = torch.empty((n2, ld), dtype=torch.int32, device=F.device)
+    if dom_count is None:
+        dom_count = torch.empty(n2, dtype=torch.int32, device=F.device)
+    nbytes = emo_workspace_size(EMO_OP_DOMINANCE_WS, n2, m, 0)
+    wsp = None
+    if nbytes:
+        ws = _ws(nbytes, ws, F.device)
+        wsp = _ptr(ws)
+    _check(lib().emo_dominance_ws(_ptr(F), n2, m, _ptr(D), D.shape[1], _ptr(dom_count), wsp, nbytes,
+                                  _stream(stream)), "emo_dominance_ws")
     return D, dom_count
 
 

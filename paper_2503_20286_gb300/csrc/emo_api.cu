@@ -318,6 +318,17 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
     sm.mark("prep");
     if (coop((const void*)k_sort, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("sort");
+    if (nprob == 1 && ins[0].mode == MODE_DOM) {  // caller-order dominance matrix only
+        const ProbIn& in = ins[0];
+        const long long nitems = cdiv(in.n2, kColBlock) * cdiv(cdiv(in.n2, 32), in.dom_chunk);
+        if (launch_dominance_caller(in.m, plan, di.sms, s, nitems, &plan->dom_ctr[0]) != cudaSuccess)
+            return EMO_ERR_CUDA;
+        sm.mark("dominance");
+        // status word of the workspace and the sticky device status
+        if (coop((const void*)k_finish, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("finish");
+        return EMO_OK;
+    }
     if (nprob == 1 && ins[0].ranked) {  // the ranks are given: no dominance matrix, no peeling
         if (coop((const void*)k_rank_in, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
         sm.mark("rank_in");
@@ -418,6 +429,12 @@ size_t emo_workspace_size(int op, int64_t n2, int32_t m, int32_t n_r)
 {
     if (!sizes_ok(n2, m)) return 0;
     if (op == EMO_OP_DOMINANCE) return 0;
+    if (op == EMO_OP_DOMINANCE_WS) {
+        if (m > 5) return 0;  // the direct kernel needs no workspace
+        ProbIn in = make_in(nullptr, nullptr, n2, m, 1, n2, 0, 0, nullptr, nullptr, MODE_DOM);
+        const int64_t b = problem_bytes(in);
+        return b < 0 ? 0 : (size_t)(kPlanBytes + b);
+    }
     if (op == EMO_OP_SELECT_RANKED) {
         if (n_r < 1) return 0;
         ProbIn in = make_in(nullptr, nullptr, n2, m, n_r, n2, 0, 0, nullptr, nullptr, MODE_SELECT);
@@ -458,6 +475,26 @@ emo_status emo_dominance_cols(const float* F, int64_t n2, int32_t m, int64_t col
     if (launch_dominance_full_c(F, n2, col_lo, col_hi, m, D, ld_words, dom_count, di.sms, s) != cudaSuccess)
         return EMO_ERR_CUDA;
     return EMO_OK;
+}
+
+emo_status emo_dominance_ws(const float* F, int64_t n2, int32_t m, uint32_t* D, int64_t ld_words, int32_t* dom_count,
+                            void* ws, size_t ws_bytes, emo_stream_t stream)
+{
+    if (!F || !D || !sizes_ok(n2, m) || ld_words < cdiv(n2, 32)) return EMO_ERR_INVALID_ARG;
+    if (m > 5) return emo_dominance_cols(F, n2, m, 0, n2, D, ld_words, dom_count, stream);
+    if (!aligned(F, 4) || !aligned(D, 4) || (dom_count && !aligned(dom_count, 4))) return EMO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dom_count && cudaMemsetAsync(dom_count, 0, (size_t)n2 * 4, s) != cudaSuccess) return EMO_ERR_CUDA;
+    const int64_t wfull = cdiv(n2, kColBlock) * 32;  // words the kernel writes per row
+    if (ld_words > wfull &&
+        cudaMemset2DAsync(D + wfull, (size_t)ld_words * 4, 0, (size_t)(ld_words - wfull) * 4, (size_t)n2, s) !=
+            cudaSuccess)
+        return EMO_ERR_CUDA;
+    std::vector<ProbIn> ins(1, make_in(F, nullptr, n2, m, 1, n2, 0, 0, nullptr, nullptr, MODE_DOM));
+    ins[0].dom_out = D;
+    ins[0].dom_count = dom_count;
+    ins[0].dom_ld = ld_words;
+    return run(ins, ws, ws_bytes, s);
 }
 
 emo_status emo_dominance(const float* F, int64_t n2, int32_t m, uint32_t* D, int64_t ld_words, int32_t* dom_count,

@@ -43,7 +43,7 @@ constexpr int kRadix = 1 << kRadixBits;
 constexpr int64_t kMaxN2 = int64_t(1) << 21;
 constexpr int32_t kNotRanked = EMO_NOT_RANKED;
 
-enum Mode : int32_t { MODE_RANK = 1, MODE_SELECT = 2, MODE_HYPE = 3 };
+enum Mode : int32_t { MODE_RANK = 1, MODE_SELECT = 2, MODE_HYPE = 3, MODE_DOM = 4 };
 
 // What the host knows about one problem.
 struct ProbIn {
@@ -72,6 +72,9 @@ struct ProbIn {
     int32_t cap_narrow;      // most CTAs of the sort / statistics / CSR / niching / survivor groups; 0 = no cap
     int32_t ranked;          // MODE_SELECT from the given ranks rank_in (no dominance matrix, no peeling)
     const int32_t* rank_in;  // [n2] caller-order ranks (EMO_NOT_RANKED beyond the last needed front)
+    uint32_t* dom_out;       // MODE_DOM: [n2][dom_ld] caller-order dominance matrix
+    int32_t* dom_count;      // MODE_DOM: [n2] dominator counts (nullable)
+    int64_t dom_ld;          // MODE_DOM: words per row
 };
 
 // Per-problem scalars; zeroed by the prep kernel.
@@ -146,7 +149,11 @@ struct ProbDev {
     int32_t* elist;          // [n_r] references served in a level
     int32_t* flag;           // [n2] survivor flags / scan scratch
     int32_t* hist;           // [G][256] radix histograms, reused by the scans
-    unsigned char* colpre;   // [ncb][m-1] column-block prefix sets (colprep_obj_bytes each)
+    unsigned char* colpre;   // [ncb][K] column-block prefix sets (colprep_obj_bytes each; K = m - 1 key
+                             // objectives, or all m of the caller-order columns in MODE_DOM)
+    float* ckeys;            // MODE_DOM: [n2p][m] objectives in caller order (padding -inf)
+    int32_t* spos;           // MODE_DOM: [2][n2] run of identical points of each caller index: first
+                             // sorted position (-1 when alone), one past the last
 };
 
 struct Plan {
@@ -238,7 +245,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
     int64_t o_front_n = take(3 * ncb * 4);
     int64_t o_wdone = take(2 * ncb * 4);
     int64_t o_wcnt = take((n2 + 2) * 4);
-    int64_t o_wofs = in.ranked ? 0 : take(ncb * (n2 + 2) * 2);
+    int64_t o_wofs = (in.ranked || in.mode == MODE_DOM) ? 0 : take(ncb * (n2 + 2) * 2);
     int64_t o_slist = take(n2 * 4);
     int64_t o_hist = take(int64_t(G) * kRadix * 4);
     int64_t o_flag = take((n2p + 1) * 4);
@@ -274,8 +281,11 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
     }
     // the prefix sets, the dominance tiles and the wavefront offsets are not
     // needed when the ranks are given
-    int64_t o_colpre = in.ranked ? 0 : take(ncb * (m - 1) * colprep_obj_bytes((int)(m - 1)));
-    int64_t o_D = in.ranked ? 0 : take(ntiles * 4096);
+    const int64_t kobj = in.mode == MODE_DOM ? m : m - 1;  // objectives with prefix sets
+    int64_t o_colpre = in.ranked ? 0 : take(ncb * kobj * colprep_obj_bytes((int)kobj));
+    int64_t o_D = (in.ranked || in.mode == MODE_DOM) ? 0 : take(ntiles * 4096);
+    int64_t o_ckeys = in.mode == MODE_DOM ? take(n2p * m * 4) : 0;
+    int64_t o_spos = in.mode == MODE_DOM ? take(2 * n2 * 4) : 0;
     if (base && d) {
         d->in = in;
         d->nrb = (int32_t)nrb;
@@ -295,7 +305,7 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         d->wdone = (int32_t*)(base + o_wdone);
         d->wmaxf = d->wdone + ncb;
         d->wcnt = (int32_t*)(base + o_wcnt);
-        d->wofs = in.ranked ? nullptr : (uint16_t*)(base + o_wofs);
+        d->wofs = (in.ranked || in.mode == MODE_DOM) ? nullptr : (uint16_t*)(base + o_wofs);
         d->slist = (int32_t*)(base + o_slist);
         d->hist = (int32_t*)(base + o_hist);
         d->flag = (int32_t*)(base + o_flag);
@@ -317,7 +327,9 @@ __host__ __device__ inline int64_t layout_problem(const ProbIn& in, int G, char*
         d->rsort = in.mode == MODE_SELECT ? (float*)(base + o_rsort) : nullptr;
         d->flagged_bound = in.mode == MODE_SELECT ? (float*)(base + o_fbound) : nullptr;
         d->colpre = in.ranked ? nullptr : (unsigned char*)(base + o_colpre);
-        d->D = in.ranked ? nullptr : (uint32_t*)(base + o_D);
+        d->D = (in.ranked || in.mode == MODE_DOM) ? nullptr : (uint32_t*)(base + o_D);
+        d->ckeys = in.mode == MODE_DOM ? (float*)(base + o_ckeys) : nullptr;
+        d->spos = in.mode == MODE_DOM ? (int32_t*)(base + o_spos) : nullptr;
     }
     return off;
 }

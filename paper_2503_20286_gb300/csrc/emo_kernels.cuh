@@ -123,6 +123,30 @@ struct VCount {
             c = t;
         }
     }
+    // add8 for a whole warp (every lane calls it): the carry out of the
+    // eights plane is rippled into the higher planes only when some lane has
+    // one (sparse inputs rarely carry that far).
+    __device__ __forceinline__ void add8_warp(const uint32_t* x)
+    {
+        uint32_t twosA, twosB, foursA, foursB, eightsA;
+        csa(twosA, ones, ones, x[0], x[1]);
+        csa(twosB, ones, ones, x[2], x[3]);
+        csa(foursA, twos, twos, twosA, twosB);
+        csa(twosA, ones, ones, x[4], x[5]);
+        csa(twosB, ones, ones, x[6], x[7]);
+        csa(foursB, twos, twos, twosA, twosB);
+        csa(eightsA, fours, fours, foursA, foursB);
+        uint32_t c = eightsA, t;
+        t = eights & c; eights ^= c; c = t;
+        if (__any_sync(0xffffffffu, c != 0u)) {
+#pragma unroll
+            for (int i = 0; i < NH; ++i) {
+                t = hi[i] & c;
+                hi[i] ^= c;
+                c = t;
+            }
+        }
+    }
     __device__ __forceinline__ void add1(uint32_t x)
     {
         uint32_t c = x, t;
@@ -212,6 +236,10 @@ cudaError_t launch_dominance_tri_range(int m, Plan* plan, int sms, cudaStream_t 
                                        unsigned long long* counter, int pfirst, int plast);
 cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, cudaStream_t s);
 cudaError_t launch_colprep(Plan* plan, int sms, cudaStream_t s, int nprob);
+// MODE_DOM (one problem, m <= 5): caller-order keys, prefix sets of every
+// objective, then the full matrix by prefix sets over `nitems` items.
+cudaError_t launch_dominance_caller(int m, Plan* plan, int sms, cudaStream_t s, long long nitems,
+                                    unsigned long long* counter);
 cudaError_t launch_dominance_full_c(const float* F, int64_t n2, int64_t col_lo, int64_t col_hi, int m, uint32_t* D,
                                     int64_t ld, int32_t* cnt, int sms, cudaStream_t s);
 

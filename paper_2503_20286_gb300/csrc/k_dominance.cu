@@ -119,7 +119,11 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
     for (int p = pfirst; p < plast; ++p) {
         const ProbDev& d = plan->p[p];
         if (ld_volatile(&d.sc->status) != 0) continue;
-        const int K = d.in.m - 1;
+        // key objectives 2..m of the lexicographic order, or every objective
+        // of the caller-order columns (MODE_DOM)
+        const bool caller = d.in.mode == MODE_DOM;
+        const int K = caller ? d.in.m : d.in.m - 1;
+        const float* const kv = caller ? d.ckeys : d.keys;
         const PrefGeom G(K);
         const int ncp1 = kHalf >> G.log_cps;  // checkpoints after the first
         const long long items = (long long)d.ncb * K;
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
             const int cb = (int)(it / K), k = (int)(it % K);
             unsigned char* blk = d.colpre + ((int64_t)cb * K + k) * G.obj_bytes;
             for (int q = tid; q < kColBlock; q += blockDim.x) {
-                s_v[q] = d.keys[((int64_t)cb * kColBlock + q) * K + k];
+                s_v[q] = kv[((int64_t)cb * kColBlock + q) * K + k];
                 s_i[q] = (uint16_t)q;
             }
             __syncthreads();
@@ -305,8 +309,8 @@ __device__ __forceinline__ void pref_rows(const unsigned char* __restrict__ obj,
             xl[jj] = (uint32_t)word;
             xh[jj] = (uint32_t)(word >> 32);
         }
-        vlo.add8(xl);
-        vhi.add8(xh);
+        vlo.add8_warp(xl);
+        vhi.add8_warp(xh);
     }
 }
 
@@ -437,6 +441,182 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
     }
 }
 
+// ------------------------------------------------------------ k_dom_caller
+// The full dominance matrix in the caller's order (emo_dominance_ws) by the
+// same prefix sets, built over caller-order column blocks for all K = m
+// objectives: the set {q : f_k(q) >= f_k(p) for every k} is the AND of K
+// prefix sets, and p dominates q iff q is in that set and is not identical to
+// p (all equal: p itself and its exact duplicates, found as the runs of the
+// lexicographic sort). Items: (column block, chunk of row blocks) over the
+// whole square; a half-warp builds one 1024-column row segment at a time
+// (a lane owns 64 columns), written into row p of D; column counts as in
+// k_dom_pref. m <= 5 (the blocks' prefix data must fit in shared memory).
+// Set-up of the caller-order matrix after the sort: the objectives in the
+// caller's order padded with -inf to whole column blocks (the prefix sets of
+// every objective are built on them), and each point's run of identical
+// points in sorted positions (first, one past the last; first = -1 when the
+// point has no duplicate).
+__global__ void k_dom_keys(Plan* plan)
+{
+    const ProbDev& d = plan->p[0];
+    if (d.in.mode != MODE_DOM || ld_volatile(&d.sc->status) != 0) return;
+    const int m = d.in.m;
+    const int64_t n2 = d.in.n2;
+    const int32_t* idx = d.idx + (int64_t)ld_volatile(&d.sc->idx_buf) * d.n2p;
+    const int32_t* rs = d.runstart;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.n2p * m; e += stride)
+        d.ckeys[e] = e / m < n2 ? d.in.F[e] + 0.0f : -INFINITY;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n2; s += stride) {
+        const int r0 = rs[s];
+        int r1 = (int)s + 1;
+        while (r1 < n2 && rs[r1] == r0) ++r1;
+        const int q = idx[s];
+        d.spos[q] = (r1 - r0 > 1) ? r0 : -1;
+        d.spos[n2 + q] = r1;
+    }
+}
+
+template <int K>
+struct CallerSmem {
+    alignas(128) unsigned char obj[K * PrefShape<K>::OBJ_BYTES];
+    int32_t cnt[kColBlock];
+    uint64_t bar;
+    long long item;
+    int skip;
+};
+
+template <int K>
+__global__ void __launch_bounds__(512, 1) k_dom_caller(Plan* plan, long long nitems, unsigned long long* counter)
+{
+    constexpr int NW = 16;
+    using S = PrefShape<K>;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    CallerSmem<K>& sm = *reinterpret_cast<CallerSmem<K>*>(smraw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int l = lane & 15, h = lane >> 4;
+    const unsigned psel = (l >> 3) ? 0x4432u : 0x4410u;  // byte selector of the lane's half count
+    if (tid == 0) mbar_init(&sm.bar, 1);
+    __syncthreads();
+    uint32_t parity = 0;
+    const ProbDev& d = plan->p[0];
+    const int64_t n2 = d.in.n2, ld = d.in.dom_ld;
+    const int nrb = d.nrb;
+    const int rows = d.in.dom_chunk;
+    const long long per_cb = cdiv(nrb, rows);
+    const bool st64 = (ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(d.in.dom_out) & 7) == 0);
+    const int32_t* const idx = d.idx + (int64_t)ld_volatile(&d.sc->idx_buf) * d.n2p;
+    const int32_t* const spos = d.spos;
+    const float* const ck = d.ckeys;
+    uint32_t* const Dout = d.in.dom_out;
+    while (true) {
+        if (tid == 0) sm.item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long item = sm.item;
+        if (item >= nitems) break;
+        const int cb = (int)(item / per_cb), chunk = (int)(item % per_cb);
+        if (tid == 0) {
+            sm.skip = ld_volatile(&d.sc->status) != 0;
+            if (!sm.skip) {
+                fence_proxy_async_smem();
+                bulk_load(sm.obj, d.colpre + (int64_t)cb * (K * S::OBJ_BYTES), (uint32_t)(K * S::OBJ_BYTES), &sm.bar);
+            }
+        }
+        for (int i = tid; i < kColBlock; i += blockDim.x) sm.cnt[i] = 0;
+        __syncthreads();
+        if (sm.skip) break;
+        if (!mbar_wait(&sm.bar, parity, kCopyWaitCycles)) {
+            if (tid == 0) set_status(d.sc, EMO_ERR_TIMEOUT);
+            mbar_wait(&sm.bar, parity, kCopyWaitCycles);
+            break;
+        }
+        parity ^= 1u;
+        const int64_t cbase = (int64_t)cb * kColBlock;
+        const int rb_lo = chunk * rows, rb_hi = min(nrb, rb_lo + rows);
+        VCount<kDomNH> vlo, vhi;
+        // keys and duplicate run of the lane's row in the warp's next row block (prefetched)
+        float key[K];
+        int nlo = -1, nhi = 0;
+        {
+            const int64_t pn = (int64_t)(rb_lo + warp) * kTileRows + lane;
+            const bool ok = rb_lo + warp < rb_hi && pn < n2;
+#pragma unroll
+            for (int k = 0; k < K; ++k) key[k] = ok ? __ldg(&ck[pn * K + k]) : 0.0f;
+            if (ok) {
+                nlo = __ldg(&spos[pn]);
+                nhi = __ldg(&spos[n2 + pn]);
+            }
+        }
+        for (int rb = rb_lo + warp; rb < rb_hi; rb += NW) {
+            const int64_t pl = (int64_t)rb * kTileRows + lane;  // the lane's row (search)
+            int t[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) t[k] = pl < n2 ? count_ge_halves(sm.obj + k * S::OBJ_BYTES, key[k]) : 0;
+            // duplicates of the lane's row: sorted positions [dup_lo, dup_hi) when it has any
+            const int dup_lo = nlo >= 0 ? nlo : 0, dup_hi = nlo >= 0 ? nhi : 0;
+            {
+                const int rbn = rb + NW;
+                const int64_t pn = (int64_t)rbn * kTileRows + lane;
+                const bool ok = rbn < rb_hi && pn < n2;
+#pragma unroll
+                for (int k = 0; k < K; ++k) key[k] = ok ? __ldg(&ck[pn * K + k]) : 0.0f;
+                nlo = ok ? __ldg(&spos[pn]) : -1;
+                nhi = ok ? __ldg(&spos[n2 + pn]) : 0;
+            }
+#pragma unroll 1
+            for (int g = 0; g < 2; ++g) {
+                uint32_t xl[8], xh[8];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = g * 8 + jj, i = j + 16 * h;  // row of the block this half-warp builds
+                    const int64_t p = (int64_t)rb * kTileRows + i;
+                    unsigned long long word = ~0ull;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const int tk = (int)__byte_perm((unsigned)__shfl_sync(0xffffffffu, t[k], i), 0u, psel);
+                        word &= prefix_word<S::LOG_CPS, S::ORD_OFF>(sm.obj + k * S::OBJ_BYTES, tk, l);
+                    }
+                    // not identical to p: p itself, and its duplicates
+                    const int dlo = __shfl_sync(0xffffffffu, dup_lo, i), dhi = __shfl_sync(0xffffffffu, dup_hi, i);
+                    if (dhi > dlo) {
+                        for (int r = dlo; r < dhi; ++r) {
+                            const int64_t off = (int64_t)__ldg(&idx[r]) - cbase - 64 * l;
+                            if (off >= 0 && off < 64) word &= ~(1ull << off);
+                        }
+                    } else {
+                        const int64_t off = p - cbase - 64 * l;
+                        if (off >= 0 && off < 64) word &= ~(1ull << off);
+                    }
+                    if (p >= n2) word = 0ull;
+                    if (p < n2) {  // words past ld (a short last block) are not stored
+                        const int64_t w0 = (int64_t)cb * 32 + 2 * l;
+                        uint32_t* dst = Dout + p * ld + w0;
+                        if (st64 && w0 + 1 < ld) {
+                            __stcs(reinterpret_cast<unsigned long long*>(dst), word);
+                        } else {
+                            if (w0 < ld) __stcs(dst, (uint32_t)word);
+                            if (w0 + 1 < ld) __stcs(dst + 1, (uint32_t)(word >> 32));
+                        }
+                    }
+                    xl[jj] = (uint32_t)word;
+                    xh[jj] = (uint32_t)(word >> 32);
+                }
+                vlo.add8_warp(xl);
+                vhi.add8_warp(xh);
+            }
+        }
+        // column counts of the item: shared-memory reduction, one global atomic per column
+        flush_counts(vlo, vhi, sm.cnt, lane);
+        __syncthreads();
+        if (d.in.dom_count)
+            for (int q = tid; q < kColBlock; q += blockDim.x) {
+                const int c = sm.cnt[(q & 31) * 32 + (q >> 5)];
+                if (c && cbase + q < n2) atomicAdd(&d.in.dom_count[cbase + q], c);
+            }
+        __syncthreads();
+    }
+}
+
 // Runtime-K variant for m >= 7 (compact code: loops over the key objectives
 // are not unrolled; the packed half counts of a row block are staged in
 // shared memory).
@@ -525,8 +705,8 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref_rt(Plan* plan, long long it
                     xl[jj] = (uint32_t)word;
                     xh[jj] = (uint32_t)(word >> 32);
                 }
-                vlo.add8(xl);
-                vhi.add8(xh);
+                vlo.add8_warp(xl);
+                vhi.add8_warp(xh);
             }
             __syncwarp();
         }
@@ -690,6 +870,39 @@ static cudaError_t launch_full_m(const float* F, int64_t n2, int64_t col_lo, int
     if (grid > nitems) grid = nitems;
     k_dom_full<M><<<(unsigned)grid, 256, smem, s>>>(F, n2, col_lo, col_hi, D, ld, cnt, nitems);
     return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t launch_caller_k(Plan* plan, int sms, cudaStream_t s, long long nitems, unsigned long long* counter)
+{
+    const size_t smem = sizeof(CallerSmem<K>);
+    cudaError_t e = cudaFuncSetAttribute(k_dom_caller<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dom_caller<K>, 512, smem);
+    if (e != cudaSuccess) return e;
+    long long grid = (long long)sms * (occ > 0 ? occ : 1);
+    if (grid > nitems) grid = nitems;
+    if (grid < 1) return cudaSuccess;
+    k_dom_caller<K><<<(unsigned)grid, 512, smem, s>>>(plan, nitems, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dominance_caller(int m, Plan* plan, int sms, cudaStream_t s, long long nitems,
+                                    unsigned long long* counter)
+{
+    k_dom_keys<<<sms * 2, 256, 0, s>>>(plan);
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
+    e0 = launch_colprep(plan, sms, s, 1);
+    if (e0 != cudaSuccess) return e0;
+    switch (m) {
+    case 2: return launch_caller_k<2>(plan, sms, s, nitems, counter);
+    case 3: return launch_caller_k<3>(plan, sms, s, nitems, counter);
+    case 4: return launch_caller_k<4>(plan, sms, s, nitems, counter);
+    case 5: return launch_caller_k<5>(plan, sms, s, nitems, counter);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 #define EMO_FOR_EACH_M(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
