@@ -239,6 +239,53 @@ emo_status emo_nsga3_select_ranked(const float* F, int64_t n2, int32_t m, const 
                                    int32_t* survivors, emo_select_info* info, void* ws, size_t ws_bytes,
                                    emo_stream_t stream);
 
+/*
+ * The two halves of emo_nsga3_select_ranked for a population split over
+ * several GPUs, each GPU owning the points [col_lo, col_hi) of the caller
+ * order (Section IV-A "Association" and "Niche Count Calculation": the
+ * association is independent per point, the niche counts are sums over the
+ * points of P = {rank < l}, so the GPUs associate their own points and add
+ * up their counts).
+ *
+ * emo_nsga3_associate_range: the normalisation over all of S = {rank <= l}
+ * (every GPU computes the same ideal point, extreme points and intercepts
+ * from the whole F, as emo_nsga3_select does), then the association of the
+ * points of S in [col_lo, col_hi) only. Arguments F .. rank as for
+ * emo_nsga3_select_ranked (no seed: nothing random happens here). Outputs
+ * (device): pi int32 [col_hi - col_lo], the associated reference of point
+ * col_lo + i, -1 outside S; dist double [col_hi - col_lo], its FP64
+ * perpendicular distance, NaN outside S; rho int32 [n_r], the niche counts of
+ * the range's points of P. pi and dist may be null when col_lo == col_hi.
+ * The values are those emo_nsga3_select computes for these points. info
+ * (nullable, device): last_rank, n_before, n_last, fallback_used and n_fronts
+ * of the whole population, n_recheck over the range, n_levels 0. ws of
+ * emo_workspace_size(EMO_OP_SELECT_RANKED, n2, m, n_r) bytes.
+ *
+ * emo_nsga3_niche_given: the niche selection and the survivors (Algorithm
+ * S.1 from its niche counts; the selection of emo_nsga3_select with
+ * niche_mode) from the association gathered from the GPUs: rank as above;
+ * rho int32 [n_r], the niche counts of all of P (the sum of every GPU's rho);
+ * last int32 [n_last], the members of front l in ascending caller order (the
+ * concatenation of the GPUs' members when they own increasing ranges),
+ * last_pi int32 [n_last] and last_dist double [n_last], their references
+ * and distances. survivors int32 [n_keep] and info as for
+ * emo_nsga3_select_ex; the survivors are those of emo_nsga3_select_ranked on
+ * the same ranks. Checked on the device (EMO_ERR_INVALID_ARG): n_last = |L|,
+ * last strictly ascending with every member of rank l, references in
+ * [0, n_r), distances finite and non-negative, counts non-negative and
+ * adding up to |P|. ws of emo_workspace_size(EMO_OP_SELECT_RANKED, n2, 2,
+ * n_r) bytes (no objectives are read).
+ */
+emo_status emo_nsga3_associate_range(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
+                                     int64_t n_keep, const int32_t* rank, int64_t col_lo, int64_t col_hi,
+                                     int32_t* pi, double* dist, int32_t* rho, emo_select_info* info, void* ws,
+                                     size_t ws_bytes, emo_stream_t stream);
+emo_status emo_nsga3_niche_given(int64_t n2, int32_t n_r, int64_t n_keep, uint64_t seed, uint64_t generation,
+                                 int32_t niche_mode, const int32_t* rank, const int32_t* rho, const int32_t* last,
+                                 const int32_t* last_pi, const double* last_dist, int64_t n_last,
+                                 int32_t* survivors, emo_select_info* info, void* ws, size_t ws_bytes,
+                                 emo_stream_t stream);
+
 /* As emo_nsga3_select, also writing the intermediates named in `dbg` (a
  * host pointer to a struct of device pointers, nullable). */
 emo_status emo_nsga3_select_debug(const float* F, int64_t n2, int32_t m, const float* R,
@@ -388,7 +435,7 @@ emo_status emo_nsga3_generation(float* X, float* F, int64_t n, int64_t d, int32_
  * allocate device memory (a plug-in whose host owns every allocation, a loop
  * that must not enter an allocator, a fixed memory budget). The paper has no
  * counterpart; this is a deployment convenience. The selection runs in an
- * 8 MiB scratch array built into the library (held on every GPU that loads
+ * 9 MiB scratch array built into the library (held on every GPU that loads
  * it until the process exits); populations with n2 <= 7168 and n_r <= 7168
  * (any m <= 16) always fit on devices with up to 304 SMs, and n2 <= 8192
  * with n_r <= 8192 (m <= 8) on devices with up to 152 SMs (the workspace

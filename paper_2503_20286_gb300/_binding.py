@@ -89,6 +89,12 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             L.emo_nsga3_select_ranked.restype = ctypes.c_int
             L.emo_nsga3_select_ranked.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp, vp, vp, sz, vp]
             L.emo_nd_rank.restype = ctypes.c_int
+            L.emo_nsga3_associate_range.restype = ctypes.c_int
+            L.emo_nsga3_associate_range.argtypes = [vp, i64, i32, vp, i32, i64, vp, i64, i64, vp, vp, vp, vp, vp, sz,
+                                                    vp]
+            L.emo_nsga3_niche_given.restype = ctypes.c_int
+            L.emo_nsga3_niche_given.argtypes = [i64, i32, i64, u64, u64, i32, vp, vp, vp, vp, vp, i64, vp, vp, vp, sz,
+                                                vp]
             L.emo_nd_rank.argtypes = [vp, i64, i32, i64, vp, vp, vp, sz, vp]
             L.emo_nsga3_select.restype = ctypes.c_int
             L.emo_nsga3_select.argtypes = [vp, i64, i32, vp, i32, i64, u64, u64, vp, vp, vp, sz, vp]
@@ -253,6 +259,48 @@ def emo_nsga3_select_ranked(F: torch.Tensor, R: torch.Tensor, n_keep: int, seed:
     _check(lib().emo_nsga3_select_ranked(_ptr(F), n2, m, _ptr(R), n_r, n_keep, seed & 0xFFFFFFFFFFFFFFFF,
                                          generation & 0xFFFFFFFFFFFFFFFF, _ptr(rank), _ptr(survivors), _ptr(info),
                                          _ptr(ws), nbytes, _stream(stream)), "emo_nsga3_select_ranked")
+    return survivors
+
+
+def emo_nsga3_associate_range(F: torch.Tensor, R: torch.Tensor, n_keep: int, rank: torch.Tensor, col_lo: int,
+                              col_hi: int, info: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                              stream=None):
+    """Association of the points [col_lo, col_hi) of a population with given
+    ranks (one GPU of a split population): (pi, dist, rho) of that range."""
+    n2, m = F.shape
+    n_r = R.shape[0]
+    k = col_hi - col_lo
+    pi = torch.empty(max(k, 0), dtype=torch.int32, device=F.device)
+    dist = torch.empty(max(k, 0), dtype=torch.float64, device=F.device)
+    rho = torch.empty(n_r, dtype=torch.int32, device=F.device)
+    nbytes = emo_workspace_size(EMO_OP_SELECT_RANKED, n2, m, n_r)
+    if nbytes == 0:
+        raise EmoError(1, "emo_workspace_size")
+    ws = _ws(nbytes, ws, F.device)
+    _check(lib().emo_nsga3_associate_range(_ptr(F), n2, m, _ptr(R), n_r, n_keep, _ptr(rank), col_lo, col_hi,
+                                           _ptr(pi) if k > 0 else None, _ptr(dist) if k > 0 else None, _ptr(rho),
+                                           _ptr(info), _ptr(ws), nbytes, _stream(stream)),
+           "emo_nsga3_associate_range")
+    return pi, dist, rho
+
+
+def emo_nsga3_niche_given(n2: int, n_r: int, n_keep: int, seed: int, generation: int, rank: torch.Tensor,
+                          rho: torch.Tensor, last: torch.Tensor, last_pi: torch.Tensor, last_dist: torch.Tensor,
+                          niche_mode: int = 0, survivors: torch.Tensor | None = None,
+                          info: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """Niching and survivors from the association gathered over the GPUs of a
+    split population (niche counts of P, front l with references and
+    distances, ascending)."""
+    if survivors is None:
+        survivors = torch.empty(n_keep, dtype=torch.int32, device=rank.device)
+    nbytes = emo_workspace_size(EMO_OP_SELECT_RANKED, n2, 2, n_r)
+    if nbytes == 0:
+        raise EmoError(1, "emo_workspace_size")
+    ws = _ws(nbytes, ws, rank.device)
+    _check(lib().emo_nsga3_niche_given(n2, n_r, n_keep, seed & 0xFFFFFFFFFFFFFFFF, generation & 0xFFFFFFFFFFFFFFFF,
+                                       niche_mode, _ptr(rank), _ptr(rho), _ptr(last), _ptr(last_pi),
+                                       _ptr(last_dist), last.numel(), _ptr(survivors), _ptr(info), _ptr(ws), nbytes,
+                                       _stream(stream)), "emo_nsga3_niche_given")
     return survivors
 
 

@@ -109,8 +109,8 @@ DevInfo dev_info()
         const void* kernels[] = {(const void*)k_sort,  (const void*)k_peel,  (const void*)k_peel_wave,
                                  (const void*)k_stats, (const void*)k_csr,   (const void*)k_niche,
                                  (const void*)k_niche_oneshot, (const void*)k_hype, (const void*)k_finish,
-                                 (const void*)k_rank_in};
-        const int dyn[] = {0, kPeelDynSmem, kPeelWaveDynSmem, 0, 0, 0, 0, 0, 0, 0};
+                                 (const void*)k_rank_in, (const void*)k_assoc_out, (const void*)k_given_in};
+        const int dyn[] = {0, kPeelDynSmem, kPeelWaveDynSmem, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int i = 0; i < (int)(sizeof(dyn) / sizeof(dyn[0])); ++i) {
             int o = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernels[i], kCoopThreads, dyn[i]) != cudaSuccess)
@@ -238,12 +238,22 @@ Shape shape_for(int dev, int sms, int m, int64_t n2)
     return sh;
 }
 
+emo_status run_niche_stages(std::vector<ProbIn>& ins, const DevInfo& di, Plan* plan, cudaStream_t s,
+                            StageMarker& sm, bool finish);
+
 // The selection stages after the peeling (statistics, association, niche
-// counts, niching, survivors); with `finish`, also the survivors' stage.
+// counts, niching, survivors); with `finish`, also the survivors' stage. A
+// population split over GPUs stops after the association of one GPU's points
+// (SPLIT_ASSOC) or starts from the gathered association (SPLIT_NICHE).
 emo_status run_selection_stages(std::vector<ProbIn>& ins, const DevInfo& di, Plan* plan, int dev, cudaStream_t s,
-                                StageMarker& sm, bool finish = true)
+                                StageMarker& sm, bool finish = true, int split = SPLIT_NONE)
 {
     const int nprob = (int)ins.size();
+    if (split == SPLIT_NICHE) {
+        if (coop((const void*)k_given_in, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("given");
+        return run_niche_stages(ins, di, plan, s, sm, finish);
+    }
     if (coop((const void*)k_stats, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("stats");
     std::vector<int> m_of(nprob);
@@ -257,6 +267,22 @@ emo_status run_selection_stages(std::vector<ProbIn>& ins, const DevInfo& di, Pla
     k_rescan<<<di.sms * 2, 256, 0, s>>>(plan);
     if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("rescan");
+    if (split == SPLIT_ASSOC) {
+        if (coop((const void*)k_assoc_out, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+        sm.mark("assoc_out");
+        if (finish) {  // status and info
+            if (coop((const void*)k_finish, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+            sm.mark("finish");
+        }
+        return EMO_OK;
+    }
+    return run_niche_stages(ins, di, plan, s, sm, finish);
+}
+
+// Niche counts and candidate lists, niching, survivors.
+emo_status run_niche_stages(std::vector<ProbIn>& ins, const DevInfo& di, Plan* plan, cudaStream_t s,
+                            StageMarker& sm, bool finish)
+{
     if (coop((const void*)k_csr, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("csr");
     bool any_exact = false, any_oneshot = false;
@@ -276,8 +302,12 @@ emo_status run_selection_stages(std::vector<ProbIn>& ins, const DevInfo& di, Pla
 
 // Launch the whole pipeline for problems already laid out in `ins` (ordered
 // by objective count).
-emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t s)
+emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t s, const SplitArgs* split = nullptr)
 {
+    SplitArgs sp;
+    std::memset(&sp, 0, sizeof(sp));
+    if (split) sp = *split;
+    if (sp.kind != SPLIT_NONE && (ins.size() != 1 || !ins[0].ranked)) return EMO_ERR_INVALID_ARG;
     DevInfo di = dev_info();
     if (!di.ok) return EMO_ERR_CUDA;
     const int nprob = (int)ins.size();
@@ -311,12 +341,14 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
     char* base = (char*)ws;
 
     StageMarker sm(s);
-    k_setup<<<1, 128, 0, s>>>(args, plan, base);
+    k_setup<<<1, 128, 0, s>>>(args, sp, plan, base);
     if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
     k_prep<<<dim3((unsigned)std::max(1, di.sms * 2 / nprob), nprob), 256, 0, s>>>(plan);
     if (cudaGetLastError() != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("prep");
-    if (coop((const void*)k_sort, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
+    // (from given ranks only the references are ordered; the niching from a
+    // given association has none)
+    if (sp.kind != SPLIT_NICHE && coop((const void*)k_sort, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("sort");
     if (nprob == 1 && ins[0].mode == MODE_DOM) {  // caller-order dominance matrix only
         const ProbIn& in = ins[0];
@@ -332,7 +364,7 @@ emo_status run(std::vector<ProbIn>& ins, void* ws, size_t ws_bytes, cudaStream_t
     if (nprob == 1 && ins[0].ranked) {  // the ranks are given: no dominance matrix, no peeling
         if (coop((const void*)k_rank_in, di.G, 0, s, plan) != cudaSuccess) return EMO_ERR_CUDA;
         sm.mark("rank_in");
-        return run_selection_stages(ins, di, plan, dev, s, sm);
+        return run_selection_stages(ins, di, plan, dev, s, sm, true, sp.kind);
     }
     if (launch_colprep(plan, di.sms, s, nprob) != cudaSuccess) return EMO_ERR_CUDA;
     sm.mark("colprep");
@@ -670,6 +702,62 @@ emo_status emo_nsga3_select_ranked(const float* F, int64_t n2, int32_t m, const 
     ins[0].ranked = 1;
     ins[0].rank_in = rank;
     return run(ins, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+emo_status emo_nsga3_associate_range(const float* F, int64_t n2, int32_t m, const float* R, int32_t n_r,
+                                     int64_t n_keep, const int32_t* rank, int64_t col_lo, int64_t col_hi, int32_t* pi,
+                                     double* dist, int32_t* rho, emo_select_info* info, void* ws, size_t ws_bytes,
+                                     emo_stream_t stream)
+{
+    if (!F || !R || !rank || !rho) return EMO_ERR_INVALID_ARG;
+    if (!sizes_ok(n2, m) || n_r < 1 || n_keep < 1 || n_keep > n2) return EMO_ERR_INVALID_ARG;
+    if (col_lo < 0 || col_lo > col_hi || col_hi > n2) return EMO_ERR_INVALID_ARG;
+    if (col_hi > col_lo && (!pi || !dist)) return EMO_ERR_INVALID_ARG;
+    if (!aligned(F, 4) || !aligned(R, 4) || !aligned(rank, 4) || !aligned(rho, 4) || !aligned(pi, 4) ||
+        !aligned(dist, 8))
+        return EMO_ERR_INVALID_ARG;
+    std::vector<ProbIn> ins(1, make_in(F, R, n2, m, n_r, n_keep, 0, 0, nullptr, info, MODE_SELECT));
+    ins[0].ranked = 1;
+    ins[0].rank_in = rank;
+    SplitArgs sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.kind = SPLIT_ASSOC;
+    sp.col_lo = col_lo;
+    sp.col_hi = col_hi;
+    sp.pi_out = pi;
+    sp.d_out = dist;
+    sp.rho = rho;
+    return run(ins, ws, ws_bytes, (cudaStream_t)stream, &sp);
+}
+
+emo_status emo_nsga3_niche_given(int64_t n2, int32_t n_r, int64_t n_keep, uint64_t seed, uint64_t generation,
+                                 int32_t niche_mode, const int32_t* rank, const int32_t* rho, const int32_t* last,
+                                 const int32_t* last_pi, const double* last_dist, int64_t n_last,
+                                 int32_t* survivors, emo_select_info* info, void* ws, size_t ws_bytes,
+                                 emo_stream_t stream)
+{
+    if (!rank || !rho || !last || !last_pi || !last_dist || !survivors) return EMO_ERR_INVALID_ARG;
+    if (!sizes_ok(n2, 2) || n_r < 1 || n_keep < 1 || n_keep > n2 || n_last < 1 || n_last > n2)
+        return EMO_ERR_INVALID_ARG;
+    if (niche_mode != EMO_NICHE_EXACT && niche_mode != EMO_NICHE_ONESHOT) return EMO_ERR_INVALID_ARG;
+    if (!aligned(rank, 4) || !aligned(rho, 4) || !aligned(last, 4) || !aligned(last_pi, 4) ||
+        !aligned(last_dist, 8) || !aligned(survivors, 4))
+        return EMO_ERR_INVALID_ARG;
+    // no objectives: the layout of two (the smallest)
+    std::vector<ProbIn> ins(1, make_in(nullptr, nullptr, n2, 2, n_r, n_keep, seed, generation, survivors, info,
+                                       MODE_SELECT));
+    ins[0].ranked = 1;
+    ins[0].rank_in = rank;
+    ins[0].niche = niche_mode;
+    SplitArgs sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.kind = SPLIT_NICHE;
+    sp.rho = const_cast<int32_t*>(rho);  // read only in this kind
+    sp.last = last;
+    sp.last_pi = last_pi;
+    sp.last_d = last_dist;
+    sp.n_last = n_last;
+    return run(ins, ws, ws_bytes, (cudaStream_t)stream, &sp);
 }
 
 emo_status emo_front_counts(const uint32_t* D, int64_t ld_words, int64_t ncols, const int32_t* rows, int64_t n_rows,

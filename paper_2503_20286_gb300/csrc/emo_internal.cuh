@@ -105,6 +105,7 @@ struct Scal {
     int32_t nsel;            // one-shot niching: references that took their nearest candidate
     int32_t longrun;         // sort: a run of equal f_1 longer than the in-place fix-up handles
     int32_t lfinal1;         // wavefront peeling: l + 1 once known, 0 before
+    unsigned long long rho_sum;  // niching from a given association: sum of the given niche counts
 };
 
 // Device-side descriptor with every workspace pointer of one problem.
@@ -156,6 +157,24 @@ struct ProbDev {
                              // sorted position (-1 when alone), one past the last
 };
 
+// A population split over several GPUs (one problem per call, ranks given):
+// the association of one GPU's points, or the niching from the association
+// gathered from all of them.
+enum SplitKind : int32_t { SPLIT_NONE = 0, SPLIT_ASSOC = 1, SPLIT_NICHE = 2 };
+struct SplitArgs {
+    int32_t kind;
+    int32_t pad_;
+    int64_t col_lo, col_hi;  // SPLIT_ASSOC: the caller indices associated
+    int32_t* pi_out;         // SPLIT_ASSOC: [col_hi - col_lo] reference, -1 outside S
+    double* d_out;           // SPLIT_ASSOC: [col_hi - col_lo] FP64 distance, NaN outside S
+    int32_t* rho;            // SPLIT_ASSOC: output [n_r] niche counts of P in the range;
+                             // SPLIT_NICHE: input [n_r] niche counts of all of P
+    const int32_t* last;     // SPLIT_NICHE: [n_last] front l, ascending caller indices
+    const int32_t* last_pi;  // SPLIT_NICHE: [n_last] their references
+    const double* last_d;    // SPLIT_NICHE: [n_last] their FP64 distances
+    int64_t n_last;
+};
+
 struct Plan {
     int32_t nprob;
     int32_t G;               // CTAs of every cooperative launch
@@ -165,10 +184,10 @@ struct Plan {
     long long dom_item_start[kMaxBatch + 1];
     long long dom_items;
     unsigned long long dom_ctr[kMaxM + 1];  // dynamic work counters per objective count
-    long long asc_item_start[kMaxBatch + 1];
-    unsigned long long asc_next;          // zeroed by the peel
+    unsigned long long asc_next[kMaxM + 1];  // tile counters of the all-reference association, per m
     int32_t status;                       // OR of problem statuses
     int32_t pad_;
+    SplitArgs split;                      // problem 0 of a one-problem call
     ProbDev p[kMaxBatch];
 };
 
@@ -362,7 +381,6 @@ __host__ __device__ inline bool dom_chunk_ok(int64_t chunk)
     return chunk >= kDomChunkMin && chunk <= kDomRowChunk && (chunk & (chunk - 1)) == 0;
 }
 
-constexpr int kAscPointsPerItem = 2048;
 
 }  // namespace emo
 

@@ -201,7 +201,7 @@ struct VCount {
 };
 
 // ------------------------------------------------------- kernels
-__global__ void k_setup(SetupArgs a, Plan* plan, char* ws);
+__global__ void k_setup(SetupArgs a, SplitArgs sp, Plan* plan, char* ws);
 __global__ void k_prep(Plan* plan);
 __global__ void k_sort(Plan* plan);
 __global__ void k_peel(Plan* plan);
@@ -217,6 +217,8 @@ __host__ __device__ constexpr int peel_smem_bytes(int ncb)
 }
 __global__ void k_peel_wave(Plan* plan);
 __global__ void k_rank_in(Plan* plan);
+__global__ void k_assoc_out(Plan* plan);
+__global__ void k_given_in(Plan* plan);
 cudaError_t launch_front_counts(const uint32_t* D, int64_t ld, int64_t ncols, const int32_t* rows, int64_t n_rows,
                                 int32_t* counts, uint8_t* new_front, int sms, cudaStream_t s);
 __host__ __device__ constexpr int peel_wave_smem_bytes(int ncb) { return peel_smem_bytes(ncb) + 2 * ncb * (int)sizeof(int); }

@@ -5,7 +5,7 @@
 // a real-time loop that must not enter the driver's allocator, or a process
 // whose memory budget is fixed up front. emo_nsga3_select_noalloc serves them
 // by running the selection in a scratch area that is part of the library
-// image itself: a file-scope device array of kScratchBytes (8 MiB). Every
+// image itself: a file-scope device array of kScratchBytes (9 MiB). Every
 // GPU on which the library is loaded holds that array until the process
 // exits. Only inputs and outputs come from the caller.
 //
@@ -23,7 +23,7 @@
 
 namespace {
 
-constexpr size_t kScratchBytes = size_t(8) << 20;
+constexpr size_t kScratchBytes = size_t(9) << 20;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];

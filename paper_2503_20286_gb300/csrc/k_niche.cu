@@ -33,10 +33,18 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_csr(Plan* plan)
     const int64_t t0 = (int64_t)g.rank * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)g.size * blockDim.x;
 
-    // niche counts of P = {rank < l}
-    for (int64_t i = t0; i < nS; i += stride) {
-        const int v = d.slist[i];
-        if (d.rank_o[v] < l) atomicAdd(&d.rho[d.pi[v]], 1);
+    // niche counts of P = {rank < l} (given, summed over the GPUs, for the
+    // niching of a split population: they must add up to |P|)
+    if (plan->split.kind == SPLIT_NICHE) {
+        if (__ldcg(&sc->rho_sum) != (unsigned long long)__ldcg(&sc->nP)) {  // both from earlier launches
+            if (g.rank == 0 && threadIdx.x == 0) set_status(sc, EMO_ERR_INVALID_ARG);
+            return;
+        }
+    } else {
+        for (int64_t i = t0; i < nS; i += stride) {
+            const int v = d.slist[i];
+            if (d.rank_o[v] < l) atomicAdd(&d.rho[d.pi[v]], 1);
+        }
     }
     // the last front in ascending index order
     bool ok = true;
@@ -397,8 +405,11 @@ __device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, i
         if (!group_kth_key(d, g, budget, rem - 1, level_keys, sm, thresh)) return false;
     }
 
-    // (4) the picks of every reference, in level order
-    for (int64_t j = t0; j < nr; j += stride) {
+    // (4) the picks of every reference, in level order; references dealt
+    // round-robin over the CTAs (each walk is sequential: spread over SMs)
+    for (int64_t jj = tid;; jj += blockDim.x) {
+        const int64_t j = jj * g.size + g.rank;
+        if (j >= nr) break;
         const int n = d.lcnt[j];
         if (n <= 0) continue;
         const int r = d.rho[j];
@@ -486,8 +497,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
             if (!group_kth_key(d, g, budget, remaining - 1, level_keys, sm, thresh)) return;
         }
 
-        // (C) picks: every level reference (all) or those with priority <= thresh
-        for (int64_t j = t0; j < nr; j += stride) {
+        // (C) picks: every level reference (all) or those with priority <= thresh;
+        // references dealt round-robin over the CTAs
+        for (int64_t jj = tid;; jj += blockDim.x) {
+            const int64_t j = jj * g.size + g.rank;
+            if (j >= nr) break;
             const int len = d.lcnt[j];
             if (len <= 0 || d.rho[j] != c) continue;
             if (!all && niche_key(seed, gen, j, c) > thresh) continue;
@@ -634,7 +648,9 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_finish(Plan* plan)
     const int64_t stride = (int64_t)g.size * blockDim.x;
     bool ok = ld_volatile(&sc->status) == 0;
     int ns = 0;
-    if (ok && (in.mode == MODE_SELECT || in.mode == MODE_HYPE)) {
+    // (the association of a split population has no survivors: its outputs
+    // were written by k_assoc_out)
+    if (ok && (in.mode == MODE_SELECT || in.mode == MODE_HYPE) && plan->split.kind != SPLIT_ASSOC) {
         const int l = sc->l;
         ns = group_compact(
             d, g, budget, n2, [&](int64_t i) { return __ldcg(&d.rank_o[i]) < l || __ldcg(&d.flag[i]) != 0; },

@@ -15,7 +15,7 @@ namespace emo {
 
 // One thread per problem: carve the workspace, zero the scalars; thread 0
 // then splits the cooperative grid into CTA groups and counts work items.
-__global__ void k_setup(SetupArgs a, Plan* plan, char* ws)
+__global__ void k_setup(SetupArgs a, SplitArgs sp, Plan* plan, char* ws)
 {
     const int t = threadIdx.x;
     if (t < a.nprob) {
@@ -30,8 +30,9 @@ __global__ void k_setup(SetupArgs a, Plan* plan, char* ws)
         plan->nprob = a.nprob;
         plan->G = a.G;
         plan->spin_budget = a.spin_budget;
+        plan->split = sp;
         for (int i = 0; i <= kMaxM; ++i) plan->dom_ctr[i] = 0;
-        plan->asc_next = 0;
+        for (int i = 0; i <= kMaxM; ++i) plan->asc_next[i] = 0;
         plan->status = 0;
         // Wide CTA groups (peeling, TensorHypE) proportional to n2^2 (the
         // dominance and peeling work), at least one CTA each and at most the
@@ -62,16 +63,13 @@ __global__ void k_setup(SetupArgs a, Plan* plan, char* ws)
         }
         plan->grp_first[a.nprob] = acc;
         plan->grpn_first[a.nprob] = accn;
-        long long di = 0, ai = 0;
+        long long di = 0;
         for (int p = 0; p < a.nprob; ++p) {
             plan->dom_item_start[p] = di;
             di += dom_items_of(a.in[p].n2, a.in[p].dom_chunk);
-            plan->asc_item_start[p] = ai;
-            if (a.in[p].mode == MODE_SELECT) ai += cdiv(a.in[p].n2, kAscPointsPerItem);
         }
         plan->dom_item_start[a.nprob] = di;
         plan->dom_items = di;
-        plan->asc_item_start[a.nprob] = ai;
     }
 }
 
@@ -84,8 +82,9 @@ __global__ void k_prep(Plan* plan)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n2 = in.n2, m = in.m;
     bool bad = false;
-    for (int64_t i = tid; i < n2 * m; i += stride)
-        if (!isfinite(in.F[i])) bad = true;
+    if (in.F)  // null only for the niching from a given association
+        for (int64_t i = tid; i < n2 * m; i += stride)
+            if (!isfinite(in.F[i])) bad = true;
     for (int64_t s = tid; s < d.n2p; s += stride) {
         d.idx[s] = (int32_t)s;
         d.cnt[s] = 0;
@@ -96,7 +95,12 @@ __global__ void k_prep(Plan* plan)
     for (int64_t c = tid; c < 3 * (int64_t)d.ncb; c += stride) d.front_n[c] = 0;
     for (int64_t c = tid; c < n2 + 2; c += stride) d.wcnt[c] = 0;  // front sizes of the wavefront peeling
     for (int64_t c = tid; c < d.ncb; c += stride) d.minrs[c] = INT32_MAX;
-    if (in.mode == MODE_SELECT) {
+    if (in.mode == MODE_SELECT && !in.R) {
+        for (int64_t j = tid; j < in.n_r; j += stride) {
+            d.rho[j] = 0;
+            d.lcnt[j] = 0;
+        }
+    } else if (in.mode == MODE_SELECT) {
         for (int64_t j = tid; j < in.n_r; j += stride) {
             double rr = 0.0;
             bool fin = true, neg = false;
@@ -118,6 +122,33 @@ __global__ void k_prep(Plan* plan)
     if (bad) set_status(d.sc, EMO_ERR_NONFINITE);
 }
 
+// References in order of their polar angle from axis 1 (the index of the
+// association scan), their angles from axes 1 and 2 and unit directions in
+// that order.
+__device__ void sort_references(const ProbDev& d, const Group& g, long long budget, RadixSmem& rsm)
+{
+    const int nr = d.in.n_r, m = d.in.m;
+    const int gr = (int)max((int64_t)1, min((int64_t)g.size, cdiv(nr, 4096)));
+    const float* rhat = d.rhat;
+    auto rkey = [&](int32_t j) { return float_key(polar_angle(rhat + (int64_t)j * m, m)); };
+    int rb = 0;
+    for (int shift = 0; shift < 32; shift += kRadixBits) {
+        bool skipped = false;
+        if (!radix_pass(d, g, gr, budget, nr, d.rord + (int64_t)rb * nr, d.rord + (int64_t)(rb ^ 1) * nr, shift, rkey,
+                        skipped, rsm))
+            return;
+        if (!skipped) rb ^= 1;
+    }
+    if (g.rank == 0 && threadIdx.x == 0) d.sc->rbuf = rb;
+    const int32_t* ro = d.rord + (int64_t)rb * nr;
+    for (int64_t s = (int64_t)g.rank * blockDim.x + threadIdx.x; s < nr; s += (int64_t)g.size * blockDim.x) {
+        const int64_t j = __ldcg(&ro[s]);
+        d.rphi[s] = polar_angle(rhat + j * m, m);
+        d.rphi2[s] = polar_angle2(rhat + j * m, m);
+        for (int k = 0; k < m; ++k) d.rsort[s * m + k] = rhat[j * m + k];
+    }
+}
+
 // Lexicographic order, sorted objective keys and runs of equal points.
 __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
 {
@@ -132,6 +163,10 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
     const int gs = (int)max((int64_t)1, min((int64_t)g.size, cdiv(n2, 4096)));
     const float* F = in.F;
     __shared__ RadixSmem rsm;
+    if (in.ranked) {  // selection from given ranks: no dominance matrix, so no point order
+        if (in.mode == MODE_SELECT) sort_references(d, g, budget, rsm);
+        return;
+    }
 
     // Lexicographic order of (f_1, ..., f_m), ties by index. First a stable
     // radix sort by f_1; then every run of equal f_1 (almost always short for
@@ -269,32 +304,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
         __syncthreads();
     }
 
-    // reference directions in order of their polar angle from axis 1 (the
-    // index of the association scan)
-    if (in.mode != MODE_SELECT) return;
     // every CTA has read the run-start carries from d.hist before the radix
-    // passes below reuse it
+    // passes of the references reuse it
+    if (in.mode != MODE_SELECT) return;
     if (!group_sync(d.sc, g.size, budget)) return;
-    const int nr = in.n_r;
-    const int gr = (int)max((int64_t)1, min((int64_t)g.size, cdiv(nr, 4096)));
-    const float* rhat = d.rhat;
-    auto rkey = [&](int32_t j) { return float_key(polar_angle(rhat + (int64_t)j * m, m)); };
-    int rb = 0;
-    for (int shift = 0; shift < 32; shift += kRadixBits) {
-        bool skipped = false;
-        if (!radix_pass(d, g, gr, budget, nr, d.rord + (int64_t)rb * nr, d.rord + (int64_t)(rb ^ 1) * nr, shift, rkey,
-                        skipped, rsm))
-            return;
-        if (!skipped) rb ^= 1;
-    }
-    if (g.rank == 0 && threadIdx.x == 0) d.sc->rbuf = rb;
-    const int32_t* ro = d.rord + (int64_t)rb * nr;
-    for (int64_t s = (int64_t)g.rank * blockDim.x + threadIdx.x; s < nr; s += (int64_t)g.size * blockDim.x) {
-        const int64_t j = __ldcg(&ro[s]);
-        d.rphi[s] = polar_angle(rhat + j * m, m);
-        d.rphi2[s] = polar_angle2(rhat + j * m, m);
-        for (int k = 0; k < m; ++k) d.rsort[s * m + k] = rhat[j * m + k];
-    }
+    sort_references(d, g, budget, rsm);
 }
 
 }  // namespace emo

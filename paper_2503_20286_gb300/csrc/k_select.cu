@@ -340,8 +340,12 @@ __global__ void __launch_bounds__(256) k_assoc_m(Plan* plan, int pfirst, int pla
         const float* __restrict__ rs = d.rsort;
         const int32_t* __restrict__ ro = d.rord + (int64_t)sc->rbuf * nr;
         const float band = assoc_band(M), margin = assoc_margin(M);
+        // a population split over GPUs associates only its own points
+        const bool ranged = plan->split.kind == SPLIT_ASSOC;
+        const int64_t lo = ranged ? plan->split.col_lo : 0, hi = ranged ? plan->split.col_hi : d.in.n2;
         for (int64_t s = (int64_t)blockIdx.x * 256 + tid; s < nS; s += (int64_t)gridDim.x * 256) {
             const int64_t v = d.slist[s];
+            if (v < lo || v >= hi) continue;
             float f[M];
             float n2 = 0.0f;
 #pragma unroll
@@ -417,6 +421,188 @@ __global__ void __launch_bounds__(256) k_assoc_m(Plan* plan, int pfirst, int pla
     }
 }
 
+// All-reference association for m >= 4, where the polar-angle index prunes
+// little: every reference is visited, uniformly across a warp. A CTA takes a
+// tile of 64 points of S (two per lane, the same in every warp) and stages
+// the unit directions in shared memory, 1024 (m <= 8) or 512 at a time; warp
+// w visits the w-th eighth of each staged block for the tile's points,
+// keeping the three smallest FP32 distances and the references of the two
+// smallest; the eight warps' lists are merged and the decision is the one of
+// k_assoc_m (two candidates inside the FP32 band: FP64 decision; three or
+// more: the point is re-scanned in FP64 by k_rescan over every reference).
+// Which reference of an FP32 tie is kept does not matter: tied candidates
+// are inside the band together. Tiles are taken from a counter, problems
+// with the most references first. (A per-point angular filter on the
+// projection f.u before the distance was measured slower: the 64 points of
+// a warp rarely all skip the same reference, and the warp runs the distance
+// whenever one of them does not.)
+constexpr int kBfWarps = 8;
+constexpr int kBfPPL = 2;                    // points per lane
+constexpr int kBfTile = 32 * kBfPPL;         // points per CTA tile
+constexpr int kBfStageBytes = 32768;         // staged unit directions
+
+struct BfTop {
+    float c1, c2, c3;
+    int s1, s2;
+    __device__ __forceinline__ void init() { c1 = c2 = c3 = INFINITY; s1 = s2 = -1; }
+    __device__ __forceinline__ void add(float dd, int j)
+    {
+        if (dd < c3) {
+            if (dd < c2) {
+                c3 = c2;
+                if (dd < c1) { c2 = c1; s2 = s1; c1 = dd; s1 = j; }
+                else { c2 = dd; s2 = j; }
+            } else {
+                c3 = dd;
+            }
+        }
+    }
+};
+
+template <int M>
+__global__ void __launch_bounds__(kBfWarps * 32) k_assoc_all(Plan* plan, int pfirst, int plast)
+{
+    constexpr int MP = (M + 3) / 4 * 4;  // padded to whole float4
+    constexpr int kStage = kBfStageBytes / (MP * 4);
+    constexpr int kPerWarp = (kStage + kBfWarps - 1) / kBfWarps;
+    __shared__ float4 s_u[kStage * MP / 4];
+    __shared__ float s_c[3][kBfWarps][kBfTile];
+    __shared__ int s_s[2][kBfWarps][kBfTile];
+    __shared__ int s_ord[kMaxBatch], s_first[kMaxBatch + 1];
+    __shared__ int s_np, s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {  // problems of this m, most references first; tile prefix
+        int np = 0;
+        for (int p = pfirst; p < plast; ++p) {
+            const ProbDev& d = plan->p[p];
+            if (d.in.mode != MODE_SELECT || d.in.m != M || ld_volatile(&d.sc->status) != 0) continue;
+            int i = np++;
+            while (i > 0 && plan->p[s_ord[i - 1]].in.n_r < d.in.n_r) { s_ord[i] = s_ord[i - 1]; --i; }
+            s_ord[i] = p;
+        }
+        s_first[0] = 0;
+        for (int i = 0; i < np; ++i)
+            s_first[i + 1] = s_first[i] + (int)cdiv(ld_volatile(&plan->p[s_ord[i]].sc->nS), kBfTile);
+        s_np = np;
+    }
+    __syncthreads();
+    const int np = s_np, ntiles = s_first[np];
+    for (;;) {
+        if (tid == 0) s_tile = (int)atomicAdd(&plan->asc_next[M], 1ull);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();  // every thread has read s_tile
+        if (t >= ntiles) break;
+        int pi_ = 0;
+        while (s_first[pi_ + 1] <= t) ++pi_;
+        const ProbDev& d = plan->p[s_ord[pi_]];
+        const Scal* sc = d.sc;
+        const int nS = ld_volatile(&sc->nS), nr = d.in.n_r;
+        const bool ranged = plan->split.kind == SPLIT_ASSOC;
+        const int64_t lo = ranged ? plan->split.col_lo : 0, hi = ranged ? plan->split.col_hi : d.in.n2;
+        const int64_t s0 = (int64_t)(t - s_first[pi_]) * kBfTile;
+        float f[kBfPPL][M];
+        float nrm[kBfPPL];
+        int64_t v[kBfPPL];
+        bool act[kBfPPL];
+        BfTop top[kBfPPL];
+#pragma unroll
+        for (int i = 0; i < kBfPPL; ++i) {
+            const int64_t s = s0 + i * 32 + lane;
+            v[i] = s < nS ? (int64_t)d.slist[s] : -1;
+            act[i] = v[i] >= lo && v[i] < hi;
+            float n2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                f[i][k] = act[i] ? (d.in.F[v[i] * M + k] - sc->z[k]) * sc->inv_a32[k] : 0.0f;
+                n2 = fmaf(f[i][k], f[i][k], n2);
+            }
+            nrm[i] = sqrtf(n2);
+            top[i].init();
+        }
+        bool scan = false;
+#pragma unroll
+        for (int i = 0; i < kBfPPL; ++i) scan |= act[i] && nrm[i] > 0.0f && isfinite(nrm[i]);
+        if (__syncthreads_or(scan)) {
+            for (int r0 = 0; r0 < nr; r0 += kStage) {
+                const int cnt = min(kStage, nr - r0);
+                __syncthreads();  // the previous block has been scanned
+                float* su = (float*)s_u;
+                for (int e = tid; e < cnt * MP; e += kBfWarps * 32) {
+                    const int q = e / MP, k = e - q * MP;
+                    su[e] = k < M ? __ldg(&d.rhat[(int64_t)(r0 + q) * M + k]) : 0.0f;
+                }
+                __syncthreads();
+                const int qa = warp * kPerWarp, qb = min(cnt, qa + kPerWarp);
+                for (int q = qa; q < qb; ++q) {
+                    float u[MP];
+#pragma unroll
+                    for (int k4 = 0; k4 < MP / 4; ++k4) {
+                        const float4 x = s_u[q * (MP / 4) + k4];
+                        u[4 * k4] = x.x;
+                        u[4 * k4 + 1] = x.y;
+                        u[4 * k4 + 2] = x.z;
+                        u[4 * k4 + 3] = x.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < kBfPPL; ++i) top[i].add(d2_f32<M>(f[i], u), r0 + q);
+                }
+            }
+        }
+        // merge the warps' lists; threads 0 .. 63 decide one point each
+#pragma unroll
+        for (int i = 0; i < kBfPPL; ++i) {
+            const int pt = i * 32 + lane;
+            s_c[0][warp][pt] = top[i].c1;
+            s_c[1][warp][pt] = top[i].c2;
+            s_c[2][warp][pt] = top[i].c3;
+            s_s[0][warp][pt] = top[i].s1;
+            s_s[1][warp][pt] = top[i].s2;
+        }
+        __syncthreads();
+        if (tid < kBfTile) {
+            const int64_t s = s0 + tid;  // point tid of the tile (lane tid & 31, slot tid >> 5)
+            const int64_t vv = s < nS ? (int64_t)d.slist[s] : -1;
+            if (vv >= lo && vv < hi) {
+                BfTop b;
+                b.init();
+                for (int w = 0; w < kBfWarps; ++w) {
+                    // the smaller two carry references; a third value only its distance
+                    b.add(s_c[0][w][tid], s_s[0][w][tid]);
+                    b.add(s_c[1][w][tid], s_s[1][w][tid]);
+                    b.add(s_c[2][w][tid], -1);
+                }
+                float ff[M], n2 = 0.0f;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    ff[k] = (d.in.F[vv * M + k] - sc->z[k]) * sc->inv_a32[k];
+                    n2 = fmaf(ff[k], ff[k], n2);
+                }
+                const float nm = sqrtf(n2);
+                const float band = assoc_band(M);
+                if (!(nm > 0.0f) || !isfinite(nm) || sqrtf(b.c3) <= sqrtf(b.c1) + band * nm) {
+                    // at the ideal point, or three or more references inside the band
+                    const int slot = atomicAdd(&d.sc->nflag, 1);
+                    d.flagged[slot] = (int32_t)vv;
+                    d.flagged_bound[slot] = INFINITY;
+                } else {
+                    const float lim = sqrtf(b.c1) + band * nm;
+                    int cand[2];
+                    int nc = 0;
+                    cand[nc++] = b.s1;
+                    if (b.s2 >= 0 && sqrtf(b.c2) <= lim) cand[nc++] = b.s2;
+                    int bj;
+                    double bd2;
+                    decide64(d, sc, vv, M, cand, nc, bj, bd2);
+                    d.pi[vv] = bj;
+                    d.d64[vv] = __dsqrt_rn(bd2);
+                }
+            }
+        }
+        __syncthreads();  // s_c / s_s are free again
+    }
+}
+
 // Points whose FP32 band holds three or more references: one warp per point
 // re-evaluates, in FP64, every reference of the scanned angular range whose
 // FP32 distance lies within the band of the range minimum.
@@ -443,7 +629,10 @@ __global__ void __launch_bounds__(256) k_rescan(Plan* plan)
                 n2 = fmaf(f[k], f[k], n2);
             }
             const float nrm = sqrtf(n2);
-            const bool all = !(bound < INFINITY) || !(nrm > 0.0f) || !isfinite(nrm);
+            // bad: at the ideal point or overflowed, every reference in FP64;
+            // otherwise the FP32 band of the range minimum filters the range
+            const bool bad = !(nrm > 0.0f) || !isfinite(nrm);
+            const bool all = bad || !(bound < INFINITY);
             int lo = 0, hi = nr;
             if (!all) {
                 const float phif = polar_angle(f, m);
@@ -462,7 +651,7 @@ __global__ void __launch_bounds__(256) k_rescan(Plan* plan)
                 return sqrtf(d2);
             };
             float dmin = INFINITY;
-            if (!all)
+            if (!bad)
                 for (int q = lo + lane; q < hi; q += 32) dmin = fminf(dmin, dist32(q));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
@@ -472,7 +661,7 @@ __global__ void __launch_bounds__(256) k_rescan(Plan* plan)
             double bd2 = INFINITY;
             int bj = INT32_MAX;
             for (int q = lo + lane; q < hi; q += 32) {
-                if (all || dist32(q) <= lim) {
+                if (bad || dist32(q) <= lim) {
                     const int j = __ldg(&ro[q]);
                     const double d2 = perp_d2(fn, d.in.R + (int64_t)j * m, m);
                     if (d2 < bd2 || (d2 == bd2 && j < bj)) { bd2 = d2; bj = j; }
@@ -503,11 +692,16 @@ cudaError_t launch_assoc(Plan* plan, int nprob, const int* m_of, int sms, int bl
         int q = p;
         while (q < nprob && m_of[q] == m_of[p]) ++q;
         const unsigned grid = (unsigned)sms * (unsigned)(blocks_per_sm > 0 ? blocks_per_sm : 8);
+        // m >= 4: every reference, tiled (tiles from a counter: a few CTAs per SM)
+        const unsigned grid_all = (unsigned)sms * 4u;
         switch (m_of[p]) {
 #define X(MM) \
     case MM: k_assoc_m<MM><<<grid, 256, 0, s>>>(plan, p, q); break;
-            X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+#define Y(MM) \
+    case MM: k_assoc_all<MM><<<grid_all, kBfWarps * 32, 0, s>>>(plan, p, q); break;
+            X(2) X(3) Y(4) Y(5) Y(6) Y(7) Y(8) Y(9) Y(10) Y(11) Y(12) Y(13) Y(14) Y(15) Y(16)
 #undef X
+#undef Y
         default: return cudaErrorInvalidValue;
         }
         cudaError_t e = cudaGetLastError();

@@ -6,7 +6,14 @@
 //     the columns whose count reaches zero (the next front there);
 //   k_rank_in -- the selection of a population whose ranks are already
 //     known (computed by the ranks together): l, |P|, |L|, the caller-order
-//     ranks and the list of S, in place of the sorting-based peeling.
+//     ranks and the list of S, in place of the sorting-based peeling;
+//   k_assoc_out -- the association step of one rank (its points of S
+//     associated after the normalisation over all of S): the references and
+//     FP64 distances of its points and the niche counts of its points of P,
+//     which the ranks add up (an all-reduce of n_r counts);
+//   k_given_in -- the niching from the gathered association: the summed
+//     niche counts and the references and distances of front l, checked
+//     against the ranks, in place of the association.
 #include <algorithm>
 
 #include "emo_kernels.cuh"
@@ -115,6 +122,82 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_rank_in(Plan* plan)
         base = __shfl_sync(0xffffffffu, base, 0);
         if (inS) d.slist[base + __popc(mask & lanemask_lt())] = (int32_t)i;
     }
+}
+
+// Outputs of the association of one rank's points [col_lo, col_hi) (narrow
+// cooperative group): reference and distance of each point of S in the
+// range, then the niche counts of the range's points of P.
+__global__ void __launch_bounds__(kCoopThreads, 1) k_assoc_out(Plan* plan)
+{
+    const Group g = group_of(plan, false);
+    if (g.prob < 0) return;  // a CTA beyond every problem's group
+    const SplitArgs& sp = plan->split;
+    const ProbDev& d = plan->p[g.prob];
+    Scal* sc = d.sc;
+    if (sp.kind != SPLIT_ASSOC || ld_volatile(&sc->status) != 0) return;
+    const int l = __ldcg(&sc->l);
+    const int64_t t0 = (int64_t)g.rank * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)g.size * blockDim.x;
+    for (int64_t i = sp.col_lo + t0; i < sp.col_hi; i += stride) {
+        const int r = __ldcg(&d.rank_o[i]);
+        const bool inS = r <= l;
+        const int p = inS ? __ldcg(&d.pi[i]) : -1;
+        sp.pi_out[i - sp.col_lo] = p;
+        sp.d_out[i - sp.col_lo] = inS ? __ldcg(&d.d64[i]) : (double)NAN;
+        if (r < l) atomicAdd(&d.rho[p], 1);
+    }
+    if (!group_sync(sc, g.size, plan->spin_budget)) return;
+    for (int64_t j = t0; j < d.in.n_r; j += stride) sp.rho[j] = __ldcg(&d.rho[j]);
+}
+
+// The association gathered from the ranks of a split population (narrow
+// cooperative group, after k_rank_in): the niche counts of P, and the
+// reference and distance of every member of front l, which must be given in
+// ascending caller order, each of rank l, |L| of them (so exactly front l).
+__global__ void __launch_bounds__(kCoopThreads, 1) k_given_in(Plan* plan)
+{
+    const Group g = group_of(plan, false);
+    if (g.prob < 0) return;  // a CTA beyond every problem's group
+    const SplitArgs& sp = plan->split;
+    const ProbDev& d = plan->p[g.prob];
+    Scal* sc = d.sc;
+    if (sp.kind != SPLIT_NICHE || ld_volatile(&sc->status) != 0) return;
+    const int l = __ldcg(&sc->l), nL = __ldcg(&sc->nL);
+    const int64_t n2 = d.in.n2;
+    const int nr = d.in.n_r;
+    const int64_t t0 = (int64_t)g.rank * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)g.size * blockDim.x;
+    if (sp.n_last != nL) {
+        if (g.rank == 0 && threadIdx.x == 0) set_status(sc, EMO_ERR_INVALID_ARG);
+        return;
+    }
+    for (int64_t t = t0; t < sp.n_last; t += stride) {
+        const int32_t v = sp.last[t];
+        const int32_t p = sp.last_pi[t];
+        const double dd = sp.last_d[t];
+        bool good = v >= 0 && v < n2 && (t == 0 || sp.last[t - 1] < v) && p >= 0 && p < nr && isfinite(dd) &&
+                    dd >= 0.0;
+        if (good) good = __ldcg(&d.rank_o[v]) == l;
+        if (!good) {
+            set_status(sc, EMO_ERR_INVALID_ARG);
+        } else {
+            d.pi[v] = p;
+            d.d64[v] = dd;
+        }
+    }
+    unsigned long long part = 0;
+    for (int64_t j = t0; j < nr; j += stride) {
+        const int32_t r = sp.rho[j];
+        if (r < 0) {
+            set_status(sc, EMO_ERR_INVALID_ARG);
+        } else {
+            d.rho[j] = r;
+            part += (unsigned long long)r;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && part) atomicAdd(&sc->rho_sum, part);
 }
 
 cudaError_t launch_front_counts(const uint32_t* D, int64_t ld, int64_t ncols, const int32_t* rows, int64_t n_rows,

@@ -14,15 +14,21 @@ after every step):
    records rank k for its members, and, unless the fronts so far already
    hold n_keep points (then l = k), ``emo_front_counts`` subtracts the
    front's rows from its columns' counts and flags the next front there;
-4. ``emo_nsga3_select_ranked`` on every rank from the ranks (normalisation,
-   association, niching and survivors are O(2N + n_r) and identical on every
-   rank, so they are replicated instead of split, which saves the collectives
-   of a split association).
+4. ``emo_nsga3_associate_range``: every rank normalises over all of S (the
+   same ideal point, extreme points and intercepts everywhere, from the
+   gathered objectives) and associates the points of S in its columns;
+   the niche counts of its points of P are summed over the ranks (an
+   all-reduce of n_r counts) and the references and distances of its
+   members of front l are all-gathered (front l is known to every rank, so
+   its members' owners are too);
+5. ``emo_nsga3_niche_given``: the niching and the survivors from the summed
+   counts and front l's association, run by every rank on the same data, so
+   every rank returns the same survivors.
 
 The exchange is written once as a generator of collective steps; ``run``
 drives it over a torch.distributed process group (NCCL between GPUs, gloo on
 CPU tensors), ``run_virtual`` drives several ranks of it in one process (the
-collectives become concatenations), which checks the same exchange on one
+collectives become lists and sums), which checks the same exchange on one
 device. The per-rank arithmetic comes from an ``ops`` object: ``GpuOps``
 calls the library's kernels; nothing here computes on the host.
 """
@@ -67,7 +73,8 @@ def unpack_bits(packed, n: int, torch):
 
 def steps(rank: int, world: int, F_own, R, n_keep: int, seed: int, generation: int, ops, torch):
     """The exchange of one rank as a generator: it yields ("all_gather", t)
-    and receives the list of every rank's t (rank order); it returns
+    and receives the list of every rank's t (rank order), or ("all_reduce",
+    t) and receives the elementwise sum over the ranks; it returns
     (survivors, info, ranks)."""
     ranges = column_ranges(int(ops.n2), world)
     lo, hi = ranges[rank]
@@ -101,7 +108,22 @@ def steps(rank: int, world: int, F_own, R, n_keep: int, seed: int, generation: i
         if ncols:
             flags = ops.front_counts(D, ncols, members, counts)
         k += 1
-    survivors, info = ops.select_ranked(F, R, n_keep, seed, generation, ranks)
+    # members is front l = k, ascending; this rank's share of it
+    pi, dist, rho = ops.associate_range(F, R, n_keep, ranks, lo, hi)
+    rho_all = yield ("all_reduce", rho)
+    own = members[(members >= lo) & (members < hi)].long() - lo
+    max_own = max(int(((members >= a) & (members < b)).sum()) for a, b in ranges)
+    pi_pad = torch.full((max_own,), -1, dtype=torch.int32, device=F.device)
+    d_pad = torch.zeros(max_own, dtype=torch.float64, device=F.device)
+    pi_pad[:own.numel()] = pi[own]
+    d_pad[:own.numel()] = dist[own]
+    pis = yield ("all_gather", pi_pad)
+    ds = yield ("all_gather", d_pad)
+    counts_l = [int(((members >= a) & (members < b)).sum()) for a, b in ranges]
+    last_pi = torch.cat([p[:c] for p, c in zip(pis, counts_l)])
+    last_d = torch.cat([x[:c] for x, c in zip(ds, counts_l)])
+    survivors, info = ops.niche_given(n2, R.shape[0], n_keep, seed, generation, ranks, rho_all, members, last_pi,
+                                      last_d)
     return survivors, info, ranks
 
 
@@ -119,6 +141,14 @@ def run(F_own, R, n_keep: int, seed: int, generation: int, ops, n2: int, group=N
     msg = next(gen)
     while True:
         op, t = msg
+        if op == "all_reduce":
+            out = t.clone()
+            dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
+            try:
+                msg = gen.send(out)
+            except StopIteration as e:
+                return e.value
+            continue
         if op != "all_gather":
             raise RuntimeError(op)
         if t.dim() == 2:  # the objectives: uneven row counts, padded to the largest
@@ -148,11 +178,18 @@ def run_virtual(F, R, n_keep: int, seed: int, generation: int, ops, world: int):
     msgs = [next(g) for g in gens]
     results = [None] * world
     while True:
+        ops_now = {m[0] for m in msgs}
+        if len(ops_now) != 1:
+            raise RuntimeError(f"ranks at different collectives: {ops_now}")
         payload = [m[1] for m in msgs]
+        if ops_now == {"all_reduce"}:
+            total = payload[0].clone()
+            for t in payload[1:]:
+                total += t
         nxt = []
         for r, g in enumerate(gens):
             try:
-                nxt.append(g.send(list(payload)))
+                nxt.append(g.send(total.clone() if ops_now == {"all_reduce"} else list(payload)))
             except StopIteration as e:
                 results[r] = e.value
                 nxt.append(None)
@@ -179,10 +216,14 @@ class GpuOps:
     def front_counts(self, D, ncols, members, counts):
         return self.emo.emo_front_counts(D, ncols, members, counts)
 
-    def select_ranked(self, F, R, n_keep, seed, generation, ranks):
+    def associate_range(self, F, R, n_keep, ranks, lo, hi):
+        return self.emo.emo_nsga3_associate_range(F, R, n_keep, ranks, lo, hi)
+
+    def niche_given(self, n2, n_r, n_keep, seed, generation, ranks, rho, last, last_pi, last_d):
         import torch
-        info = torch.zeros(8, dtype=torch.int32, device=F.device)
-        surv = self.emo.emo_nsga3_select_ranked(F, R, n_keep, seed, generation, ranks, info=info)
+        info = torch.zeros(8, dtype=torch.int32, device=ranks.device)
+        surv = self.emo.emo_nsga3_niche_given(n2, n_r, n_keep, seed, generation, ranks, rho, last, last_pi, last_d,
+                                              info=info)
         return surv, info
 
 

@@ -1,7 +1,10 @@
-"""Test-only arithmetic for the split exchange on CPU ranks: the same three
+"""Test-only arithmetic for the split exchange on CPU ranks: the same four
 steps as the library's kernels (column share of the dominance matrix and
-its counts, one peeling step, selection), written with the oracle and
-numpy. Lets gloo ranks on the CPU run paper_2503_20286_gb300.split."""
+its counts, one peeling step, the association of a column range, the
+niching from the gathered association), written with the oracle and numpy.
+Lets gloo ranks on the CPU run paper_2503_20286_gb300.split; the niching
+step checks that the exchange delivered the oracle's niche counts and front
+l."""
 import numpy as np
 import torch
 
@@ -21,6 +24,28 @@ class NumpyOps:
         counts -= d
         return ((d > 0) & (counts == 0)).to(torch.uint8)
 
-    def select_ranked(self, F, R, n_keep, seed, generation, ranks):
-        surv, _ = oracle.nsga3_select(F.numpy(), R.numpy(), n_keep, seed, generation, trace=False)
+    def associate_range(self, F, R, n_keep, ranks, lo, hi):
+        """pi, dist of the range and the niche counts of its points of P,
+        from the oracle's trace (normalisation and association draw nothing
+        random)."""
+        self._F, self._R = F.numpy(), R.numpy()
+        _, t = oracle.nsga3_select(self._F, self._R, n_keep, 0, 0)
+        r = ranks.numpy()
+        l = t["last_rank"]
+        assert np.array_equal(np.where(t["rank"] <= l, t["rank"], r), r)
+        pi = t["pi"][lo:hi].astype(np.int32)
+        P = np.nonzero(r[lo:hi] < l)[0]
+        rho = np.bincount(pi[P], minlength=R.shape[0]).astype(np.int32)
+        return torch.from_numpy(pi), torch.from_numpy(t["dist"][lo:hi].copy()), torch.from_numpy(rho)
+
+    def niche_given(self, n2, n_r, n_keep, seed, generation, ranks, rho, last, last_pi, last_d):
+        """The gathered association must be the oracle's (summed niche
+        counts of P; front l ascending with its references and distances);
+        the survivors are then the oracle's."""
+        surv, t = oracle.nsga3_select(self._F, self._R, n_keep, seed, generation)
+        L = np.nonzero(t["rank"] == t["last_rank"])[0]
+        assert np.array_equal(rho.numpy(), t["rho"])
+        assert np.array_equal(last.numpy(), L)
+        assert np.array_equal(last_pi.numpy(), t["pi"][L])
+        assert np.array_equal(last_d.numpy(), t["dist"][L])
         return torch.from_numpy(surv), None

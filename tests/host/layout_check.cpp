@@ -83,7 +83,7 @@ int main()
             if ((char*)d.D + d.ntiles * 4096 > end) return fail("D overflow", d.ntiles, bytes);
         }
     }
-    // the allocation-free entry point's 8 MiB scratch holds the plan and one
+    // the allocation-free entry point's 9 MiB scratch holds the plan and one
     // selection of 2N = n_r = 7168 at any m for cooperative launches of up
     // to 608 CTAs (304 SMs at the largest occupancy used, 2), and of
     // 2N = n_r = 8192 at m <= 8 for launches of up to 304 CTAs (152 SMs)
@@ -98,7 +98,7 @@ int main()
             in.n_r = (int32_t)n;
             in.mode = MODE_SELECT;
             const long long need = plan_bytes + layout_problem(in, big ? 304 : 608, nullptr, nullptr);
-            if (need > (8ll << 20)) return fail("no-alloc scratch", m, need);
+            if (need > (9ll << 20)) return fail("no-alloc scratch", m, need);
         }
     }
     std::printf("layout ok\n");
