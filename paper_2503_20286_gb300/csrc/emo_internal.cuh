@@ -237,9 +237,20 @@ __host__ __device__ constexpr int64_t colprep_ord_off(int K)
 {
     return kPrefPbOff + (((kColBlock / 2) >> colprep_log_cps(K)) + 1) * 32 * 4;
 }
-__host__ __device__ constexpr int64_t colprep_obj_bytes(int K)
+// Objectives with at most two prefix-set keys also carry a bucket index of
+// the block's descending values (header: lowest finite value, bucket scale;
+// then per bucket the first and one-past-last positions of the values in
+// it), which turns the search for a row's count into one lookup and a search
+// among the few values of one bucket.
+constexpr int kPrefBuckets = 4096;
+__host__ __device__ constexpr bool colprep_has_buckets(int K) { return K <= 2; }
+__host__ __device__ constexpr int64_t colprep_bkt_off(int K)
 {
     return colprep_ord_off(K) + (colprep_log_cps(K) > 0 ? kColBlock * 2 : 0);
+}
+__host__ __device__ constexpr int64_t colprep_obj_bytes(int K)
+{
+    return colprep_bkt_off(K) + (colprep_has_buckets(K) ? 128 + kPrefBuckets * 4 : 0);
 }
 
 // Byte layout of one problem region; fills `d` when base != 0. Returns the

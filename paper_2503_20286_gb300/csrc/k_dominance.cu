@@ -89,6 +89,15 @@ __device__ __forceinline__ void flush_counts(VCount<NH>& vlo, VCount<NH>& vhi, i
     vhi = VCount<NH>();
 }
 
+// Bucket of x for a block's header (lowest finite value vmin, scale > 0 or
+// 0): non-decreasing in x, the same arithmetic where the index is built and
+// where it is searched.
+__device__ __forceinline__ int pref_bucket(float x, float vmin, float scale)
+{
+    const int b = __float2int_rz(__fmul_rn(__fsub_rn(x, vmin), scale));
+    return min(max(b, 0), kPrefBuckets - 1);
+}
+
 // ------------------------------------------------------------ k_colprep
 // Slot of entry i of a block's descending values (bank-spreading swizzle).
 __device__ __forceinline__ int fv_slot(int i) { return i ^ ((i >> 5) & 31); }
@@ -115,6 +124,8 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
     __shared__ uint8_t s_mark[kColBlock];
     __shared__ uint32_t s_part[8][32];
     __shared__ int s_warp[32];
+    __shared__ float s_full[kColBlock];  // the full descending order (bucket index)
+    __shared__ float s_hdr[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int p = pfirst; p < plast; ++p) {
         const ProbDev& d = plan->p[p];
@@ -169,6 +180,42 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
                                  (q < kHalf ? count_before512<true>(s_v + kHalf, x) : count_before512<false>(s_v, x));
                 fv[fv_slot(rank)] = x;
                 s_mark[rank] = q < kHalf;
+                if (colprep_has_buckets(K)) s_full[rank] = x;
+            }
+            if (colprep_has_buckets(K)) {
+                // bucket index: header (vmin, scale), then per bucket b the
+                // positions [lo, hi) of the values whose bucket is b (the
+                // bucket is non-increasing along the descending order)
+                __syncthreads();
+                float* hdr = reinterpret_cast<float*>(blk + colprep_bkt_off(K));
+                uint32_t* tab = reinterpret_cast<uint32_t*>(blk + colprep_bkt_off(K) + 128);
+                if (tid == 0) {
+                    int nf = kColBlock;  // finite entries (padding columns hold -inf)
+                    while (nf > 1 && !(s_full[nf - 1] > -INFINITY)) --nf;
+                    const float vmax = s_full[0], vmin = s_full[nf - 1];
+                    float sc = vmax > vmin ? (float)kPrefBuckets / (vmax - vmin) : 0.0f;
+                    if (!(sc < 1e30f)) sc = 0.0f;  // overflowed span or tiny span: one bucket
+                    s_hdr[0] = vmin;
+                    s_hdr[1] = sc;
+                    hdr[0] = vmin;
+                    hdr[1] = sc;
+                }
+                __syncthreads();
+                const float vmin = s_hdr[0], sc = s_hdr[1];
+                // first position whose bucket is <= b
+                auto first_le = [&](int b) {
+                    int lo = 0, hi = kColBlock;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (pref_bucket(s_full[mid], vmin, sc) <= b) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    return lo;
+                };
+                for (int b = tid; b < kPrefBuckets; b += blockDim.x) {
+                    const int lo = first_le(b), hi = b > 0 ? first_le(b - 1) : kColBlock;
+                    tab[b] = (uint32_t)lo | ((uint32_t)hi << 16);
+                }
             }
             // interleaved prefix bitsets: lane w builds word w from the sorted
             // columns of half w / 16; warp v covers checkpoints (v*seg, (v+1)*seg]
@@ -236,6 +283,31 @@ __device__ __forceinline__ int count_ge_halves(const unsigned char* ob, float x)
     if (fv[fv_slot(pos)] >= x) ++pos;
     const int t0 = reinterpret_cast<const uint16_t*>(ob + kPrefCumOff)[pos];
     return t0 | ((pos - t0) << 16);
+}
+
+// count_ge_halves through the bucket index (objectives with at most two
+// keys): every value of a higher bucket is >= x, every value of a lower one
+// < x, so the count is the bucket's first position plus the values >= x
+// among the bucket's own (a short search, usually over one or none).
+template <int K>
+__device__ __forceinline__ int count_ge_halves_k(const unsigned char* ob, float x)
+{
+    if constexpr (!colprep_has_buckets(K)) {
+        return count_ge_halves(ob, x);
+    } else {
+        const float* fv = reinterpret_cast<const float*>(ob);
+        const float* hdr = reinterpret_cast<const float*>(ob + colprep_bkt_off(K));
+        const uint32_t e =
+            reinterpret_cast<const uint32_t*>(ob + colprep_bkt_off(K) + 128)[pref_bucket(x, hdr[0], hdr[1])];
+        int lo = (int)(e & 0xffffu), hi = (int)(e >> 16);
+        while (lo < hi) {  // first position of the bucket with a value < x
+            const int mid = (lo + hi) >> 1;
+            if (fv[fv_slot(mid)] >= x) lo = mid + 1;
+            else hi = mid;
+        }
+        const int t0 = reinterpret_cast<const uint16_t*>(ob + kPrefCumOff)[lo];
+        return t0 | ((lo - t0) << 16);
+    }
 }
 
 // Two words (columns 64 l .. 64 l + 63, l = lane % 16) of an objective's
@@ -422,7 +494,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
             const int64_t pl = (int64_t)rb * kTileRows + lane;
             int t[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) t[k] = pl < n2 ? count_ge_halves(sm.obj + k * S::OBJ_BYTES, key[k]) : 0;
+            for (int k = 0; k < K; ++k) t[k] = pl < n2 ? count_ge_halves_k<K>(sm.obj + k * S::OBJ_BYTES, key[k]) : 0;
             {
                 const int rbn = rb + NW;
                 const int64_t pn = (int64_t)rbn * kTileRows + lane;
@@ -551,7 +623,7 @@ __global__ void __launch_bounds__(512, 1) k_dom_caller(Plan* plan, long long nit
             const int64_t pl = (int64_t)rb * kTileRows + lane;  // the lane's row (search)
             int t[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) t[k] = pl < n2 ? count_ge_halves(sm.obj + k * S::OBJ_BYTES, key[k]) : 0;
+            for (int k = 0; k < K; ++k) t[k] = pl < n2 ? count_ge_halves_k<K>(sm.obj + k * S::OBJ_BYTES, key[k]) : 0;
             // duplicates of the lane's row: sorted positions [dup_lo, dup_hi) when it has any
             const int dup_lo = nlo >= 0 ? nlo : 0, dup_hi = nlo >= 0 ? nhi : 0;
             {
