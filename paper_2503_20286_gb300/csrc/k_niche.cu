@@ -271,6 +271,111 @@ __device__ __forceinline__ void niche_pick(const ProbDev& d, const int32_t* L, u
     fen_remove(d.fen + off, full, pos);
 }
 
+// The picks of one reference by a whole warp (lists of at most
+// kWarpPickMax members): the list's remaining members as bit masks in
+// registers (lane i holds list positions [32 R i, 32 R (i + 1)), R words),
+// rebuilt from the survivor flags; each pick finds the member of rank
+// (u len) >> 32 among the remaining ones by a warp scan of the lanes' counts
+// and a bit select inside the lane that holds it. The same member as
+// niche_pick (nearest at level 0, else the same rank among the remaining
+// members in list order) and the same draws, without the Fenwick tree's
+// dependent loads. Returns false on an inconsistent count.
+constexpr int kWarpPickWords = 4;
+constexpr int kWarpPickMax = 32 * 32 * kWarpPickWords;
+
+__device__ __forceinline__ int select_bit(uint32_t w, int k)  // position of the k-th set bit
+{
+    int bit = 0;
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const int c = __popc(w & ((1u << sh) - 1u));
+        if (k >= c) {
+            k -= c;
+            w >>= sh;
+            bit += sh;
+        }
+    }
+    return bit;
+}
+
+__device__ bool warp_picks(const ProbDev& d, const int32_t* L, uint64_t seed, uint64_t gen, int64_t j, int r, int n,
+                           int take, int lane)
+{
+    constexpr int R = kWarpPickWords;
+    const int off = d.loff[j], full = d.loff[j + 1] - off;
+    uint32_t mask[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) mask[q] = 0u;
+    for (int base = 0; base < full; base += 32) {  // coalesced: word base / 32 of the list
+        const int pos = base + lane;
+        const bool live = pos < full && __ldcg(&d.flag[L[off + pos]]) == 0;
+        const uint32_t bal = __ballot_sync(0xffffffffu, live);
+        const int word = base >> 5, owner = word / R, wq = word - owner * R;
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (lane == owner && q == wq) mask[q] = bal;
+    }
+    for (int t = 0; t < take; ++t) {
+        const int c = r + t, len = n - t;
+        int pos;
+        if (c == 0) {  // nearest member (distance, then caller index); the list is whole at level 0
+            double bd = INFINITY;
+            int bi = INT32_MAX, bp = -1;
+            for (int q = lane; q < full; q += 32) {
+                const int v = L[off + q];
+                const double dv = d.d64[v];
+                if (dv < bd || (dv == bd && v < bi)) { bd = dv; bi = v; bp = q; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+                if (od < bd || (od == bd && oi < bi)) { bd = od; bi = oi; bp = op; }
+            }
+            pos = bp;
+        } else {
+            const uint32_t u = niche_random(seed, gen, (uint32_t)j, (uint32_t)c, 1u);
+            const int rank = (int)(((unsigned long long)u * (unsigned long long)len) >> 32);
+            int cnt = 0;
+#pragma unroll
+            for (int q = 0; q < R; ++q) cnt += __popc(mask[q]);
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const unsigned hit = __ballot_sync(0xffffffffu, inc > rank);
+            if (!hit) return false;  // fewer remaining members than len
+            const int owner = __ffs(hit) - 1;
+            int k = rank - (inc - cnt);  // rank inside the owner lane (valid there)
+            int p = 0;
+            if (lane == owner) {
+                int wq = 0;
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int cq = __popc(mask[q]);
+                    if (wq == q && k >= cq) { k -= cq; ++wq; }
+                }
+                uint32_t w = 0u;
+#pragma unroll
+                for (int q = 0; q < R; ++q)
+                    if (q == wq) w = mask[q];
+                p = (owner * R + wq) * 32 + select_bit(w, k);
+            }
+            pos = __shfl_sync(0xffffffffu, p, owner);
+        }
+        if (pos < 0 || pos >= full) return false;
+        const int word = pos >> 5, owner = word / R, wq = word - owner * R;
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (lane == owner && q == wq) mask[q] &= ~(1u << (pos & 31));
+        if (lane == 0) d.flag[L[off + pos]] = 1;
+    }
+    return true;
+}
+
 // The remaining picks in bulk (water-filling). From the current niche counts
 // rho_j and live list lengths n_j, the level form serves reference j at the
 // levels c = rho_j .. rho_j + n_j - 1 (one member per level while its list
@@ -406,15 +511,41 @@ __device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, i
     }
 
     // (4) the picks of every reference, in level order; references dealt
-    // round-robin over the CTAs (each walk is sequential: spread over SMs)
+    // round-robin over the CTAs (each walk is sequential: spread over SMs):
+    // lists of at most kWarpPickMax members one warp each, longer lists one
+    // thread each (Fenwick tree)
+    auto take_of = [&](int64_t j, int n, int r) {
+        int take = r < c_star ? min(c_star, r + n) - r : 0;
+        if (r <= c_star && c_star < r + n && (all || niche_key(seed, gen, j, c_star) <= thresh)) ++take;
+        return take;
+    };
+    {
+        const int lane = tid & 31, nw = blockDim.x >> 5;
+        for (int64_t jj = tid >> 5;; jj += nw) {
+            const int64_t j = jj * g.size + g.rank;
+            if (j >= nr) break;
+            const int n = d.lcnt[j];
+            if (n <= 0 || d.loff[j + 1] - d.loff[j] > kWarpPickMax) continue;
+            const int r = d.rho[j];
+            const int take = take_of(j, n, r);
+            if (take > 0 && !warp_picks(d, L, seed, gen, j, r, n, take, lane)) {
+                if (lane == 0) set_status(sc, EMO_ERR_INVALID_ARG);
+                continue;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                d.lcnt[j] = n - take;
+                d.rho[j] = r + take;
+            }
+        }
+    }
     for (int64_t jj = tid;; jj += blockDim.x) {
         const int64_t j = jj * g.size + g.rank;
         if (j >= nr) break;
         const int n = d.lcnt[j];
-        if (n <= 0) continue;
+        if (n <= 0 || d.loff[j + 1] - d.loff[j] <= kWarpPickMax) continue;
         const int r = d.rho[j];
-        int take = r < c_star ? min(c_star, r + n) - r : 0;
-        if (r <= c_star && c_star < r + n && (all || niche_key(seed, gen, j, c_star) <= thresh)) ++take;
+        const int take = take_of(j, n, r);
         for (int t = 0; t < take; ++t) niche_pick(d, L, seed, gen, j, r + t, n - t);
         d.lcnt[j] = n - take;
         d.rho[j] = r + take;
