@@ -126,142 +126,173 @@ __global__ void __launch_bounds__(256) k_colprep(Plan* plan, int pfirst, int pla
     __shared__ int s_warp[32];
     __shared__ float s_full[kColBlock];  // the full descending order (bucket index)
     __shared__ float s_hdr[2];
+    __shared__ int s_bh[kPrefBuckets];  // bucket histogram
+    __shared__ long long s_first[kMaxBatch + 1];  // items (column block, objective) before each problem
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int p = pfirst; p < plast; ++p) {
+    // key objectives 2..m of the lexicographic order, or every objective of
+    // the caller-order columns (MODE_DOM)
+    auto keys_of = [&](const ProbDev& d) { return d.in.mode == MODE_DOM ? d.in.m : d.in.m - 1; };
+    if (tid == 0) {
+        long long acc = 0;
+        for (int p = pfirst; p < plast; ++p) {
+            s_first[p - pfirst] = acc;
+            const ProbDev& d = plan->p[p];
+            if (ld_volatile(&d.sc->status) == 0) acc += (long long)d.ncb * keys_of(d);
+        }
+        s_first[plast - pfirst] = acc;
+    }
+    __syncthreads();
+    // the items of every problem in one sequence (a batch's small problems
+    // together fill the grid)
+    const long long total = s_first[plast - pfirst];
+    int p = pfirst;
+    for (long long it_all = blockIdx.x; it_all < total; it_all += gridDim.x) {
+        while (s_first[p + 1 - pfirst] <= it_all) ++p;
         const ProbDev& d = plan->p[p];
-        if (ld_volatile(&d.sc->status) != 0) continue;
-        // key objectives 2..m of the lexicographic order, or every objective
-        // of the caller-order columns (MODE_DOM)
         const bool caller = d.in.mode == MODE_DOM;
-        const int K = caller ? d.in.m : d.in.m - 1;
+        const int K = keys_of(d);
         const float* const kv = caller ? d.ckeys : d.keys;
         const PrefGeom G(K);
         const int ncp1 = kHalf >> G.log_cps;  // checkpoints after the first
-        const long long items = (long long)d.ncb * K;
-        for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-            const int cb = (int)(it / K), k = (int)(it % K);
-            unsigned char* blk = d.colpre + ((int64_t)cb * K + k) * G.obj_bytes;
-            for (int q = tid; q < kColBlock; q += blockDim.x) {
-                s_v[q] = kv[((int64_t)cb * kColBlock + q) * K + k];
-                s_i[q] = (uint16_t)q;
-            }
-            __syncthreads();
-            // bitonic sort: half ascending, then value descending, then local
-            // index ascending (positions 0..511 = half 0, 512..1023 = half 1)
-            for (int size = 2; size <= kColBlock; size <<= 1) {
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    for (int t = tid; t < kColBlock / 2; t += blockDim.x) {
-                        const int i = 2 * t - (t & (stride - 1)), j = i + stride;
-                        const float vi = s_v[i], vj = s_v[j];
-                        const int ii = s_i[i], ij = s_i[j];
-                        const int hi_ = ii >= kHalf, hj = ij >= kHalf;
-                        const bool j_first = hj < hi_ || (hj == hi_ && (vj > vi || (vj == vi && ij < ii)));
-                        const bool up = (i & size) == 0;
-                        if (up == j_first) {
-                            s_v[i] = vj; s_v[j] = vi;
-                            s_i[i] = (uint16_t)ij; s_i[j] = (uint16_t)ii;
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-            float* fv = reinterpret_cast<float*>(blk);
-            uint16_t* cum0 = reinterpret_cast<uint16_t*>(blk + kPrefCumOff);
-            uint32_t* pb = reinterpret_cast<uint32_t*>(blk + kPrefPbOff);
-            if (G.log_cps > 0) {
-                uint16_t* so = reinterpret_cast<uint16_t*>(blk + G.ord_off);
-                for (int q = tid; q < kColBlock; q += blockDim.x) so[q] = s_i[q];
-            }
-            // merge of the halves into the full descending order (ties: half 0
-            // first); mark the half-0 positions
-            for (int q = tid; q < kColBlock; q += blockDim.x) {
-                const float x = s_v[q];
-                const int rank = (q & (kHalf - 1)) +
-                                 (q < kHalf ? count_before512<true>(s_v + kHalf, x) : count_before512<false>(s_v, x));
-                fv[fv_slot(rank)] = x;
-                s_mark[rank] = q < kHalf;
-                if (colprep_has_buckets(K)) s_full[rank] = x;
-            }
-            if (colprep_has_buckets(K)) {
-                // bucket index: header (vmin, scale), then per bucket b the
-                // positions [lo, hi) of the values whose bucket is b (the
-                // bucket is non-increasing along the descending order)
-                __syncthreads();
-                float* hdr = reinterpret_cast<float*>(blk + colprep_bkt_off(K));
-                uint32_t* tab = reinterpret_cast<uint32_t*>(blk + colprep_bkt_off(K) + 128);
-                if (tid == 0) {
-                    int nf = kColBlock;  // finite entries (padding columns hold -inf)
-                    while (nf > 1 && !(s_full[nf - 1] > -INFINITY)) --nf;
-                    const float vmax = s_full[0], vmin = s_full[nf - 1];
-                    float sc = vmax > vmin ? (float)kPrefBuckets / (vmax - vmin) : 0.0f;
-                    if (!(sc < 1e30f)) sc = 0.0f;  // overflowed span or tiny span: one bucket
-                    s_hdr[0] = vmin;
-                    s_hdr[1] = sc;
-                    hdr[0] = vmin;
-                    hdr[1] = sc;
-                }
-                __syncthreads();
-                const float vmin = s_hdr[0], sc = s_hdr[1];
-                // first position whose bucket is <= b
-                auto first_le = [&](int b) {
-                    int lo = 0, hi = kColBlock;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (pref_bucket(s_full[mid], vmin, sc) <= b) hi = mid;
-                        else lo = mid + 1;
-                    }
-                    return lo;
-                };
-                for (int b = tid; b < kPrefBuckets; b += blockDim.x) {
-                    const int lo = first_le(b), hi = b > 0 ? first_le(b - 1) : kColBlock;
-                    tab[b] = (uint32_t)lo | ((uint32_t)hi << 16);
-                }
-            }
-            // interleaved prefix bitsets: lane w builds word w from the sorted
-            // columns of half w / 16; warp v covers checkpoints (v*seg, (v+1)*seg]
-            const int hbase = (lane >> 4) * kHalf;
-            const int seg = ncp1 / 8;
-            uint32_t part = 0u;
-            for (int c = warp * seg; c < (warp + 1) * seg; ++c)
-                for (int e = 0; e < G.cps; ++e) {
-                    const int col = s_i[hbase + c * G.cps + e];
-                    if ((col >> 5) == lane) part |= 1u << (col & 31);
-                }
-            s_part[warp][lane] = part;
-            __syncthreads();
-            uint32_t acc = 0u;
-            for (int w = 0; w < warp; ++w) acc |= s_part[w][lane];
-            if (warp == 0) pb[lane] = 0u;
-            for (int c = warp * seg; c < (warp + 1) * seg; ++c) {
-                for (int e = 0; e < G.cps; ++e) {
-                    const int col = s_i[hbase + c * G.cps + e];
-                    if ((col >> 5) == lane) acc |= 1u << (col & 31);
-                }
-                pb[(c + 1) * 32 + lane] = acc;
-            }
-            // cum0[j] = half-0 entries among the first j of the full order
-            {
-                const int j0 = tid * 4;  // 256 threads x 4 entries
-                const int m0 = s_mark[j0], m1 = s_mark[j0 + 1], m2 = s_mark[j0 + 2], m3 = s_mark[j0 + 3];
-                int tot;
-                const int ex = block_exclusive_scan<256>(m0 + m1 + m2 + m3, s_warp, tot);
-                if (tid == 0) cum0[0] = 0;
-                cum0[j0 + 1] = (uint16_t)(ex + m0);
-                cum0[j0 + 2] = (uint16_t)(ex + m0 + m1);
-                cum0[j0 + 3] = (uint16_t)(ex + m0 + m1 + m2);
-                cum0[j0 + 4] = (uint16_t)(ex + m0 + m1 + m2 + m3);
-            }
-            __syncthreads();
+        const long long it = it_all - s_first[p - pfirst];
+        const int cb = (int)(it / K), k = (int)(it % K);
+        unsigned char* blk = d.colpre + ((int64_t)cb * K + k) * G.obj_bytes;
+        for (int q = tid; q < kColBlock; q += blockDim.x) {
+            s_v[q] = kv[((int64_t)cb * kColBlock + q) * K + k];
+            s_i[q] = (uint16_t)q;
         }
+        __syncthreads();
+        // bitonic sort: half ascending, then value descending, then local
+        // index ascending (positions 0..511 = half 0, 512..1023 = half 1)
+        for (int size = 2; size <= kColBlock; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = tid; t < kColBlock / 2; t += blockDim.x) {
+                    const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+                    const float vi = s_v[i], vj = s_v[j];
+                    const int ii = s_i[i], ij = s_i[j];
+                    const int hi_ = ii >= kHalf, hj = ij >= kHalf;
+                    const bool j_first = hj < hi_ || (hj == hi_ && (vj > vi || (vj == vi && ij < ii)));
+                    const bool up = (i & size) == 0;
+                    if (up == j_first) {
+                        s_v[i] = vj; s_v[j] = vi;
+                        s_i[i] = (uint16_t)ij; s_i[j] = (uint16_t)ii;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        float* fv = reinterpret_cast<float*>(blk);
+        uint16_t* cum0 = reinterpret_cast<uint16_t*>(blk + kPrefCumOff);
+        uint32_t* pb = reinterpret_cast<uint32_t*>(blk + kPrefPbOff);
+        if (G.log_cps > 0) {
+            uint16_t* so = reinterpret_cast<uint16_t*>(blk + G.ord_off);
+            for (int q = tid; q < kColBlock; q += blockDim.x) so[q] = s_i[q];
+        }
+        // merge of the halves into the full descending order (ties: half 0
+        // first); mark the half-0 positions
+        for (int q = tid; q < kColBlock; q += blockDim.x) {
+            const float x = s_v[q];
+            const int rank = (q & (kHalf - 1)) +
+                             (q < kHalf ? count_before512<true>(s_v + kHalf, x) : count_before512<false>(s_v, x));
+            fv[fv_slot(rank)] = x;
+            s_mark[rank] = q < kHalf;
+            if (colprep_has_buckets(K)) s_full[rank] = x;
+        }
+        if (colprep_has_buckets(K)) {
+            // bucket index: header (vmin, scale), then per bucket b the
+            // positions [lo, hi) of the values whose bucket is b (the
+            // bucket is non-increasing along the descending order)
+            __syncthreads();
+            float* hdr = reinterpret_cast<float*>(blk + colprep_bkt_off(K));
+            uint32_t* tab = reinterpret_cast<uint32_t*>(blk + colprep_bkt_off(K) + 128);
+            if (tid == 0) {
+                int nf = kColBlock;  // finite entries (padding columns hold -inf)
+                while (nf > 1 && !(s_full[nf - 1] > -INFINITY)) --nf;
+                const float vmax = s_full[0], vmin = s_full[nf - 1];
+                float sc = vmax > vmin ? (float)kPrefBuckets / (vmax - vmin) : 0.0f;
+                if (!(sc < 1e30f)) sc = 0.0f;  // overflowed span or tiny span: one bucket
+                s_hdr[0] = vmin;
+                s_hdr[1] = sc;
+                hdr[0] = vmin;
+                hdr[1] = sc;
+            }
+            __syncthreads();
+            const float vmin = s_hdr[0], sc = s_hdr[1];
+            // histogram of the values' buckets, then per bucket b:
+            // lo = #{bucket > b}, hi = #{bucket >= b} (a block scan)
+            constexpr int PER = kPrefBuckets / 256;
+            for (int b = tid; b < kPrefBuckets; b += blockDim.x) s_bh[b] = 0;
+            __syncthreads();
+            for (int q = tid; q < kColBlock; q += blockDim.x) atomicAdd(&s_bh[pref_bucket(s_full[q], vmin, sc)], 1);
+            __syncthreads();
+            int h[PER], sum = 0;
+#pragma unroll
+            for (int e = 0; e < PER; ++e) {
+                h[e] = s_bh[tid * PER + e];
+                sum += h[e];
+            }
+            int tot;
+            int below = block_exclusive_scan<256>(sum, s_warp, tot);  // #{bucket < tid * PER}
+#pragma unroll
+            for (int e = 0; e < PER; ++e) {
+                const int hi = kColBlock - below;
+                below += h[e];
+                tab[tid * PER + e] = (uint32_t)(kColBlock - below) | ((uint32_t)hi << 16);
+            }
+            __syncthreads();  // s_warp is scanned again below
+        }
+        // interleaved prefix bitsets: lane w builds word w from the sorted
+        // columns of half w / 16; warp v covers checkpoints (v*seg, (v+1)*seg]
+        const int hbase = (lane >> 4) * kHalf;
+        const int seg = ncp1 / 8;
+        uint32_t part = 0u;
+        for (int c = warp * seg; c < (warp + 1) * seg; ++c)
+            for (int e = 0; e < G.cps; ++e) {
+                const int col = s_i[hbase + c * G.cps + e];
+                if ((col >> 5) == lane) part |= 1u << (col & 31);
+            }
+        s_part[warp][lane] = part;
+        __syncthreads();
+        uint32_t acc = 0u;
+        for (int w = 0; w < warp; ++w) acc |= s_part[w][lane];
+        if (warp == 0) pb[lane] = 0u;
+        for (int c = warp * seg; c < (warp + 1) * seg; ++c) {
+            for (int e = 0; e < G.cps; ++e) {
+                const int col = s_i[hbase + c * G.cps + e];
+                if ((col >> 5) == lane) acc |= 1u << (col & 31);
+            }
+            pb[(c + 1) * 32 + lane] = acc;
+        }
+        // cum0[j] = half-0 entries among the first j of the full order
+        {
+            const int j0 = tid * 4;  // 256 threads x 4 entries
+            const int m0 = s_mark[j0], m1 = s_mark[j0 + 1], m2 = s_mark[j0 + 2], m3 = s_mark[j0 + 3];
+            int tot;
+            const int ex = block_exclusive_scan<256>(m0 + m1 + m2 + m3, s_warp, tot);
+            if (tid == 0) cum0[0] = 0;
+            cum0[j0 + 1] = (uint16_t)(ex + m0);
+            cum0[j0 + 2] = (uint16_t)(ex + m0 + m1);
+            cum0[j0 + 3] = (uint16_t)(ex + m0 + m1 + m2);
+            cum0[j0 + 4] = (uint16_t)(ex + m0 + m1 + m2 + m3);
+        }
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------------------ k_dom_pref
+// Objectives whose prefix sets have a checkpoint at every count and room in
+// shared memory (at most two keys): the rows' checkpoint offsets are staged
+// per warp in shared memory instead of being broadcast by shuffles.
+template <int K>
+constexpr bool kStageOffsets = K <= 2 && PrefShape<K>::LOG_CPS == 0;
+
 template <int K>
 struct PrefSmem {
     alignas(128) unsigned char obj[K * PrefShape<K>::OBJ_BYTES];
     alignas(128) int32_t rs[kColBlock];
     int32_t cnt[kColBlock];
+    // per warp, objective and half: byte offset t * 128 of each row's checkpoint
+    uint32_t off[kStageOffsets<K> ? 16 * K * 64 : 1];
     uint64_t bar;
     long long item;
     int skip;
@@ -377,6 +408,41 @@ __device__ __forceinline__ void pref_rows(const unsigned char* __restrict__ obj,
                 word &= prefix_word<S::LOG_CPS, S::ORD_OFF>(obj + k * S::OBJ_BYTES, tk, l);
             }
             word = row_masks<DIAG, DUP>(word, rowbase + i, cbase, rs, l);
+            __stcs(dst + j * 16, word);
+            xl[jj] = (uint32_t)word;
+            xh[jj] = (uint32_t)(word >> 32);
+        }
+        vlo.add8_warp(xl);
+        vhi.add8_warp(xh);
+    }
+}
+
+// pref_rows with the rows' checkpoint offsets read from this warp's staged
+// offsets `so` ([K][2 halves][32 rows], bytes t * 128 of the half's count):
+// one shared load per row and objective replaces a shuffle, a byte permute
+// and the offset arithmetic.
+template <int K, bool DIAG, bool DUP>
+__device__ __forceinline__ void pref_rows_off(const unsigned char* __restrict__ obj,
+                                              const int32_t* __restrict__ rs, const uint32_t* so, int64_t rowbase,
+                                              int64_t cbase, uint32_t* tile, VCount<kDomNH>& vlo,
+                                              VCount<kDomNH>& vhi, int lane)
+{
+    using S = PrefShape<K>;
+    const int l = lane & 15, h = lane >> 4;
+    const uint32_t* my = so + (l >> 3) * 32 + 16 * h;  // this lane's half; rows j + 16 h
+    const unsigned char* pb = obj + kPrefPbOff + l * 8;
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(tile + h * 16 * 32) + l;
+#pragma unroll 1
+    for (int g = 0; g < 2; ++g) {
+        uint32_t xl[8], xh[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            const int j = g * 8 + jj;
+            unsigned long long word = ~0ull;
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                word &= *reinterpret_cast<const unsigned long long*>(pb + k * S::OBJ_BYTES + my[k * 64 + j]);
+            word = row_masks<DIAG, DUP>(word, rowbase + j + 16 * h, cbase, rs, l);
             __stcs(dst + j * 16, word);
             xl[jj] = (uint32_t)word;
             xh[jj] = (uint32_t)(word >> 32);
@@ -505,9 +571,23 @@ __global__ void __launch_bounds__(512, 1) k_dom_pref(Plan* plan, long long item_
             const bool dup = rb * kTileRows + 31 >= dupcut;
             const int64_t rowbase = (int64_t)rb * kTileRows;
             uint32_t* tile = Dm + tile_index(rb, cb, ncb) * (int64_t)(kTileRows * kTileWords);
-            if (dup) pref_rows<K, true, true>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
-            else if (diag) pref_rows<K, true, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
-            else pref_rows<K, false, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
+            if constexpr (kStageOffsets<K>) {
+                uint32_t* so = sm.off + warp * (K * 64);
+                __syncwarp();  // the previous row block's offsets have been read
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    so[k * 64 + lane] = (uint32_t)(t[k] & 0xffff) * 128u;
+                    so[k * 64 + 32 + lane] = (uint32_t)(t[k] >> 16) * 128u;
+                }
+                __syncwarp();
+                if (dup) pref_rows_off<K, true, true>(sm.obj, sm.rs, so, rowbase, cbase, tile, vlo, vhi, lane);
+                else if (diag) pref_rows_off<K, true, false>(sm.obj, sm.rs, so, rowbase, cbase, tile, vlo, vhi, lane);
+                else pref_rows_off<K, false, false>(sm.obj, sm.rs, so, rowbase, cbase, tile, vlo, vhi, lane);
+            } else {
+                if (dup) pref_rows<K, true, true>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
+                else if (diag) pref_rows<K, true, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
+                else pref_rows<K, false, false>(sm.obj, sm.rs, t, rowbase, cbase, tile, vlo, vhi, lane);
+            }
         }
         dom_flush_item(d, cbase, vlo, vhi, sm.cnt, lane);
     }

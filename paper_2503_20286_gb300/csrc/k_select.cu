@@ -328,96 +328,115 @@ __device__ __forceinline__ int lower_bound_f(const float* a, int n, float x)
 template <int M>
 __global__ void __launch_bounds__(256) k_assoc_m(Plan* plan, int pfirst, int plast)
 {
+    // the points of S of every problem of this m in one sequence (a batch's
+    // small problems together fill the grid)
+    __shared__ long long s_first[kMaxBatch + 1];
     const int tid = threadIdx.x;
-    for (int p = pfirst; p < plast; ++p) {
-        const ProbDev& d = plan->p[p];
+    if (tid == 0) {
+        long long acc = 0;
+        for (int p = pfirst; p < plast; ++p) {
+            s_first[p - pfirst] = acc;
+            const ProbDev& d = plan->p[p];
+            if (d.in.mode == MODE_SELECT && d.in.m == M && ld_volatile(&d.sc->status) == 0)
+                acc += ld_volatile(&d.sc->nS);
+        }
+        s_first[plast - pfirst] = acc;
+    }
+    __syncthreads();
+    const long long total = s_first[plast - pfirst];
+    const float band = assoc_band(M), margin = assoc_margin(M);
+    // a population split over GPUs associates only its own points
+    const bool ranged = plan->split.kind == SPLIT_ASSOC;
+    for (long long gs = (long long)blockIdx.x * 256 + tid; gs < total; gs += (long long)gridDim.x * 256) {
+        int plo = 0, phi = plast - pfirst;  // last problem with s_first <= gs
+        while (phi - plo > 1) {
+            const int mid = (plo + phi) >> 1;
+            if (s_first[mid] <= gs) plo = mid;
+            else phi = mid;
+        }
+        while (s_first[plo + 1] <= gs) ++plo;  // skip problems without points
+        const ProbDev& d = plan->p[pfirst + plo];
         const Scal* sc = d.sc;
-        if (d.in.mode != MODE_SELECT || d.in.m != M || ld_volatile(&sc->status) != 0) continue;
-        const int nS = ld_volatile(&sc->nS);
+        const int64_t s = gs - s_first[plo];
         const int nr = d.in.n_r;
         const float* __restrict__ rphi = d.rphi;
         const float* __restrict__ rphi2 = d.rphi2;
         const float* __restrict__ rs = d.rsort;
         const int32_t* __restrict__ ro = d.rord + (int64_t)sc->rbuf * nr;
-        const float band = assoc_band(M), margin = assoc_margin(M);
-        // a population split over GPUs associates only its own points
-        const bool ranged = plan->split.kind == SPLIT_ASSOC;
         const int64_t lo = ranged ? plan->split.col_lo : 0, hi = ranged ? plan->split.col_hi : d.in.n2;
-        for (int64_t s = (int64_t)blockIdx.x * 256 + tid; s < nS; s += (int64_t)gridDim.x * 256) {
-            const int64_t v = d.slist[s];
-            if (v < lo || v >= hi) continue;
-            float f[M];
-            float n2 = 0.0f;
+        const int64_t v = d.slist[s];
+        if (v < lo || v >= hi) continue;
+        float f[M];
+        float n2 = 0.0f;
 #pragma unroll
-            for (int k = 0; k < M; ++k) {
-                f[k] = (d.in.F[v * M + k] - sc->z[k]) * sc->inv_a32[k];
-                n2 = fmaf(f[k], f[k], n2);
-            }
-            const float nrm = sqrtf(n2);
-            if (!(nrm > 0.0f) || !isfinite(nrm)) {  // at the ideal point (or overflow): exhaustive FP64 scan
-                const int slot = atomicAdd(&d.sc->nflag, 1);
-                d.flagged[slot] = (int32_t)v;
-                d.flagged_bound[slot] = INFINITY;
-                continue;
-            }
-            const float phif = polar_angle(f, M);
-            const float phi2f = polar_angle2(f, M);
-            float c1 = INFINITY, c2 = INFINITY, c3 = INFINITY;  // FP32 d^2, best three
-            int s1 = -1, s2 = -1;                                 // sorted positions of the best two
-            float bound = INFINITY;                               // angular half-width still to scan
-            int L = lower_bound_f(rphi, nr, phif) - 1, Rp = L + 1;
-            float dl = L >= 0 ? phif - __ldg(&rphi[L]) : INFINITY;
-            float dr = Rp < nr ? __ldg(&rphi[Rp]) - phif : INFINITY;
-            while (L >= 0 || Rp < nr) {  // at most n_r steps
-                const bool left = L >= 0 && (Rp >= nr || dl <= dr);
-                const float dm = left ? dl : dr;
-                if (!(dm <= bound)) break;
-                int q;  // 0 <= q < n_r
-                if (left) {
-                    q = L--;
-                    dl = L >= 0 ? phif - __ldg(&rphi[L]) : INFINITY;
-                } else {
-                    q = Rp++;
-                    dr = Rp < nr ? __ldg(&rphi[Rp]) - phif : INFINITY;
-                }
-                // second pivot: the angle to the reference is at least the
-                // difference of the angles from axis 2 (same margins as axis 1)
-                if (M > 2 && !(fabsf(__ldg(&rphi2[q]) - phi2f) <= bound)) continue;
-                float u[M];
-#pragma unroll
-                for (int k = 0; k < M; ++k) u[k] = __ldg(&rs[(int64_t)q * M + k]);
-                const float dd = d2_f32<M>(f, u);
-                if (dd < c3) {
-                    if (dd < c2) {
-                        c3 = c2;
-                        if (dd < c1) { c2 = c1; s2 = s1; c1 = dd; s1 = q; }
-                        else { c2 = dd; s2 = q; }
-                        // angle of the best so far, bounded from above
-                        const float sn = fminf(1.0f, sqrtf(c1) / nrm * 1.00001f + 2.0f * band);
-                        const float th = asinf(sn);
-                        bound = th + margin > kAssocMaxBound ? INFINITY : th + margin;
-                    } else {
-                        c3 = dd;
-                    }
-                }
-            }
-            const float d1 = sqrtf(c1), lim = d1 + band * nrm;
-            if (sqrtf(c3) <= lim) {  // three or more references inside the band
-                const int slot = atomicAdd(&d.sc->nflag, 1);
-                d.flagged[slot] = (int32_t)v;
-                d.flagged_bound[slot] = bound;
-                continue;
-            }
-            int cand[2];
-            int nc = 0;
-            cand[nc++] = __ldg(&ro[s1]);
-            if (s2 >= 0 && sqrtf(c2) <= lim) cand[nc++] = __ldg(&ro[s2]);
-            int bj;
-            double bd2;
-            decide64(d, sc, v, M, cand, nc, bj, bd2);
-            d.pi[v] = bj;
-            d.d64[v] = __dsqrt_rn(bd2);
+        for (int k = 0; k < M; ++k) {
+            f[k] = (d.in.F[v * M + k] - sc->z[k]) * sc->inv_a32[k];
+            n2 = fmaf(f[k], f[k], n2);
         }
+        const float nrm = sqrtf(n2);
+        if (!(nrm > 0.0f) || !isfinite(nrm)) {  // at the ideal point (or overflow): exhaustive FP64 scan
+            const int slot = atomicAdd(&d.sc->nflag, 1);
+            d.flagged[slot] = (int32_t)v;
+            d.flagged_bound[slot] = INFINITY;
+            continue;
+        }
+        const float phif = polar_angle(f, M);
+        const float phi2f = polar_angle2(f, M);
+        float c1 = INFINITY, c2 = INFINITY, c3 = INFINITY;  // FP32 d^2, best three
+        int s1 = -1, s2 = -1;                                 // sorted positions of the best two
+        float bound = INFINITY;                               // angular half-width still to scan
+        int L = lower_bound_f(rphi, nr, phif) - 1, Rp = L + 1;
+        float dl = L >= 0 ? phif - __ldg(&rphi[L]) : INFINITY;
+        float dr = Rp < nr ? __ldg(&rphi[Rp]) - phif : INFINITY;
+        while (L >= 0 || Rp < nr) {  // at most n_r steps
+            const bool left = L >= 0 && (Rp >= nr || dl <= dr);
+            const float dm = left ? dl : dr;
+            if (!(dm <= bound)) break;
+            int q;  // 0 <= q < n_r
+            if (left) {
+                q = L--;
+                dl = L >= 0 ? phif - __ldg(&rphi[L]) : INFINITY;
+            } else {
+                q = Rp++;
+                dr = Rp < nr ? __ldg(&rphi[Rp]) - phif : INFINITY;
+            }
+            // second pivot: the angle to the reference is at least the
+            // difference of the angles from axis 2 (same margins as axis 1)
+            if (M > 2 && !(fabsf(__ldg(&rphi2[q]) - phi2f) <= bound)) continue;
+            float u[M];
+#pragma unroll
+            for (int k = 0; k < M; ++k) u[k] = __ldg(&rs[(int64_t)q * M + k]);
+            const float dd = d2_f32<M>(f, u);
+            if (dd < c3) {
+                if (dd < c2) {
+                    c3 = c2;
+                    if (dd < c1) { c2 = c1; s2 = s1; c1 = dd; s1 = q; }
+                    else { c2 = dd; s2 = q; }
+                    // angle of the best so far, bounded from above
+                    const float sn = fminf(1.0f, sqrtf(c1) / nrm * 1.00001f + 2.0f * band);
+                    const float th = asinf(sn);
+                    bound = th + margin > kAssocMaxBound ? INFINITY : th + margin;
+                } else {
+                    c3 = dd;
+                }
+            }
+        }
+        const float d1 = sqrtf(c1), lim = d1 + band * nrm;
+        if (sqrtf(c3) <= lim) {  // three or more references inside the band
+            const int slot = atomicAdd(&d.sc->nflag, 1);
+            d.flagged[slot] = (int32_t)v;
+            d.flagged_bound[slot] = bound;
+            continue;
+        }
+        int cand[2];
+        int nc = 0;
+        cand[nc++] = __ldg(&ro[s1]);
+        if (s2 >= 0 && sqrtf(c2) <= lim) cand[nc++] = __ldg(&ro[s2]);
+        int bj;
+        double bd2;
+        decide64(d, sc, v, M, cand, nc, bj, bd2);
+        d.pi[v] = bj;
+        d.d64[v] = __dsqrt_rn(bd2);
     }
 }
 
