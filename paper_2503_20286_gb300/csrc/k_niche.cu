@@ -384,9 +384,13 @@ __device__ bool warp_picks(const ProbDev& d, const int32_t* L, uint64_t seed, ui
 // smallest c* with P(c*) + ne(c*) >= remaining and there serves only the
 // remaining - P(c*) references of smallest priority. Each reference then
 // makes its picks itself, in level order, with the level form's draws, so the
-// picks are the same. `handled` is false (nothing done) when the levels span
-// more than kNicheBins values; the caller then goes on level by level.
-__device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, int remaining, NicheSmem& sm,
+// picks are the same. The levels are histogrammed over a window of at most
+// kNicheBins values from c_lo (references whose interval starts beyond it
+// add nothing inside it); when c* lies beyond the window, every level of the
+// window is served in full, `remaining` drops by their picks and `handled`
+// is false (the caller goes on from the next level); otherwise remaining
+// becomes 0 and `handled` true.
+__device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, int& remaining, NicheSmem& sm,
                            const int32_t* L, int& levels, bool& handled)
 {
     Scal* sc = d.sc;
@@ -398,7 +402,7 @@ __device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, i
     const int64_t stride = (int64_t)g.size * blockDim.x;
     int32_t* hist = d.nhist;
     unsigned long long* part = reinterpret_cast<unsigned long long*>(d.nhist + kNicheBins);
-    __shared__ int s_cstar, s_pstar, s_nestar, s_lev;
+    __shared__ int s_cstar, s_pstar, s_nestar, s_lev, s_pwin;
     handled = false;
 
     // (1) the span of levels [c_lo, c_end) of the live references
@@ -428,15 +432,15 @@ __device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, i
         if (g.rank == 0 && tid == 0) set_status(sc, EMO_ERR_INVALID_ARG);
         return false;
     }
-    const int R = c_end - c_lo;
-    if (R > kNicheBins) return true;  // too wide for the histogram: level by level
+    const bool windowed = c_end - c_lo > kNicheBins;
+    const int R = windowed ? kNicheBins : c_end - c_lo;
 
-    // (2) ne(c) as a difference array over the span
+    // (2) ne(c) as a difference array over the window
     for (int64_t j = t0; j < nr; j += stride) {
         const int n = __ldcg(&d.lcnt[j]);
         if (n > 0) {
             const int r = __ldcg(&d.rho[j]) - c_lo;
-            atomicAdd(&hist[r], 1);
+            if (r < R) atomicAdd(&hist[r], 1);
             if (r + n < R) atomicAdd(&hist[r + n], -1);
         }
     }
@@ -462,7 +466,10 @@ __device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, i
             nsum += pre;
         }
         int ppre = block_exclusive_scan<kCoopThreads>(nsum, sm.warp, tot);  // P at this thread's first level
-        if (tid == 0) s_cstar = INT32_MAX;
+        if (tid == 0) {
+            s_cstar = INT32_MAX;
+            s_pwin = tot;  // picks of every level of the window
+        }
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < PER; ++e) {
@@ -489,11 +496,14 @@ __device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, i
         __syncthreads();
     }
     const int cstar = s_cstar;
-    if (cstar == INT32_MAX) {  // fewer live candidates than picks: inconsistent lists
+    const bool found = cstar != INT32_MAX;
+    if (!found && !windowed) {  // fewer live candidates than picks: inconsistent lists
         if (g.rank == 0 && tid == 0) set_status(sc, EMO_ERR_INVALID_ARG);
         return false;
     }
-    const int c_star = c_lo + cstar, rem = remaining - s_pstar, ne_star = s_nestar;
+    // not found: every level below c_lo + R in full, none at c_star itself
+    const int c_star = found ? c_lo + cstar : c_lo + R;
+    const int rem = found ? remaining - s_pstar : 0, ne_star = found ? s_nestar : 0;
     const bool all = ne_star <= rem;
     unsigned long long thresh = ~0ull;
     if (!all) {  // the rem references of smallest priority among those at level c*
@@ -516,7 +526,7 @@ __device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, i
     // thread each (Fenwick tree)
     auto take_of = [&](int64_t j, int n, int r) {
         int take = r < c_star ? min(c_star, r + n) - r : 0;
-        if (r <= c_star && c_star < r + n && (all || niche_key(seed, gen, j, c_star) <= thresh)) ++take;
+        if (found && r <= c_star && c_star < r + n && (all || niche_key(seed, gen, j, c_star) <= thresh)) ++take;
         return take;
     };
     {
@@ -552,7 +562,8 @@ __device__ bool niche_bulk(const ProbDev& d, const Group& g, long long budget, i
     }
     if (!group_sync(sc, g.size, budget)) return false;
     levels += s_lev;
-    handled = true;
+    handled = found;
+    remaining = found ? 0 : remaining - s_pwin;
     return true;
 }
 
@@ -656,7 +667,6 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_niche(Plan* plan)
         if (remaining > 0 && levels >= kNicheDirectLevels) {  // the rest in bulk when the span allows
             bool handled = false;
             if (!niche_bulk(d, g, budget, remaining, sm, L, levels, handled)) return;
-            if (handled) remaining = 0;
         }
     }
     if (g.rank == 0 && tid == 0) sc->levels = levels;

@@ -135,15 +135,17 @@ def test_select_exactly_filled_fronts():
     assert t["last_rank"] == 4 and t["n_before"] + t["n_last"] == n_keep
 
 
-@pytest.mark.parametrize("run", [3, 40])
-def test_select_ties_in_the_first_objective(run):
+@pytest.mark.parametrize("n2,m,run", [(3000, 3, 3), (3000, 3, 40), (3000, 3, 700), (3000, 3, 3000),
+                                       (10000, 3, 9000), (6000, 8, 1500), (6000, 8, 5000)])
+def test_select_ties_in_the_first_objective(n2, m, run):
     # f_1 takes each value `run` times (runs of equal f_1 in the sorted
     # order): short runs are ordered in place, a run longer than 32 makes the
     # sort fall back to the full radix sort over every objective
-    F = wl.population(3000, 3, 9, "sphere", seed=31)
+    F = wl.population(n2, m, m + 6, "sphere", seed=31 + run)
     order = np.argsort(F[:, 0], kind="stable")
-    F[order, 0] = (np.arange(3000) // run).astype(np.float32) / np.float32(1024)
-    _gpu.compare_select(F, wl.das_dennis(30, 3), 1400, seed=5)
+    F[order, 0] = (np.arange(n2) // run).astype(np.float32) / np.float32(1024)
+    R = wl.das_dennis(30, 3) if m == 3 else wl.das_dennis(3, m)
+    _gpu.compare_select(F, R, n2 * 7 // 15, seed=5)
     r, _ = _gpu.gpu_rank(F)
     assert np.array_equal(r, oracle.nd_sort_deb(F))
 
@@ -253,3 +255,23 @@ def test_many_niching_levels(n2, m, h, keep_frac, q):
     R = wl.das_dennis(h, m)
     info, t = _gpu.compare_select(F, R, int(keep_frac * n2), seed=3, gen=5)
     assert t["n_levels"] > 20
+
+
+@pytest.mark.parametrize("n_last,keep_last", [(10000, 6000), (9000, 8900)])
+def test_niching_levels_beyond_one_window(n_last, keep_last):
+    """Niche counts spread over more than 4096 levels with one reference
+    serving a pick per level: front 0 spread over the line f1 + f2 = 0.8,
+    front 1 (the last) a narrow band around the diagonal of f1 + f2 = 1, all
+    nearest the diagonal direction (21 directions). The bulk niching serves
+    a whole window of 4096 levels and goes on from the next level; picks and
+    the level count equal the oracle's."""
+    rng = np.random.default_rng(n_last)
+    x = np.sort(rng.uniform(0.0, 0.8, 2000)).astype(np.float32)
+    P = np.stack([x, np.float32(0.8) - x], axis=1)
+    a = np.float32(0.49) + np.arange(n_last, dtype=np.float32) * np.float32(0.02 / n_last)
+    Lf = np.stack([a, np.float32(1.0) - a], axis=1)
+    F = np.ascontiguousarray(np.concatenate([P, Lf])[rng.permutation(2000 + n_last)])
+    R = wl.das_dennis(20, 2)
+    info, t = _gpu.compare_select(F, R, 2000 + keep_last, seed=7, gen=2)
+    assert t["last_rank"] == 1 and t["n_last"] == n_last
+    assert t["n_levels"] > 4096
