@@ -92,6 +92,8 @@ struct Scal {
     int32_t lbuf;            // llist half holding the sorted candidate lists
     int32_t rbuf;            // rord half holding the angle order
     uint32_t zkey[kMaxM];
+    uint32_t kor[kMaxM];     // OR of the order-preserving keys of each objective over all points
+    uint32_t kinv[kMaxM];    // OR of their complements (a bit varies iff set in both)
     uint32_t asf32[kMaxM];
     unsigned long long asf64[kMaxM];
     int32_t ext[kMaxM];

@@ -82,9 +82,38 @@ __global__ void k_prep(Plan* plan)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n2 = in.n2, m = in.m;
     bool bad = false;
-    if (in.F)  // null only for the niching from a given association
-        for (int64_t i = tid; i < n2 * m; i += stride)
-            if (!isfinite(in.F[i])) bad = true;
+    if (in.F) {  // null only for the niching from a given association
+        // finiteness, and which bits of each objective's sort key vary (a
+        // radix pass over a byte that no point changes is skipped)
+        uint32_t kor[kMaxM], kinv[kMaxM];
+#pragma unroll
+        for (int k = 0; k < kMaxM; ++k) kor[k] = kinv[k] = 0u;
+        for (int64_t i = tid; i < n2; i += stride) {
+#pragma unroll
+            for (int k = 0; k < kMaxM; ++k) {
+                if (k >= m) break;
+                const float f = in.F[i * m + k];
+                if (!isfinite(f)) bad = true;
+                const uint32_t key = float_key(f);
+                kor[k] |= key;
+                kinv[k] |= ~key;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kMaxM; ++k) {
+            if (k >= m) break;
+            uint32_t a = kor[k], b = kinv[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a |= __shfl_xor_sync(0xffffffffu, a, o);
+                b |= __shfl_xor_sync(0xffffffffu, b, o);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                if (a) atomicOr(&d.sc->kor[k], a);
+                if (b) atomicOr(&d.sc->kinv[k], b);
+            }
+        }
+    }
     for (int64_t s = tid; s < d.n2p; s += stride) {
         d.idx[s] = (int32_t)s;
         d.cnt[s] = 0;
@@ -174,8 +203,12 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_sort(Plan* plan)
     // by one thread. If some run is longer than kShortRun, the full stable
     // LSD sort over all objectives runs instead (from the index order).
     int buf = 0;
+    const uint32_t* kor = d.sc->kor;  // written by k_prep
+    const uint32_t* kinv = d.sc->kinv;
     auto sort_by = [&](int k) -> bool {
+        const uint32_t varies = __ldcg(&kor[k]) & __ldcg(&kinv[k]);
         for (int shift = 0; shift < 32; shift += kRadixBits) {
+            if (((varies >> shift) & (kRadix - 1)) == 0) continue;  // every point has the same digit
             const int32_t* src = d.idx + (int64_t)buf * d.n2p;
             int32_t* dst = d.idx + (int64_t)(buf ^ 1) * d.n2p;
             bool skipped = false;
