@@ -129,13 +129,13 @@ class ClockSampler:
 
 # DRAM traffic of k_dom_pref<3> per byte of stored tiles, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum of one launch at
-# 2N=100,000, M=3: 19.12 MB read + 574.38 MB written for 635.79 MB of tiles).
+# 2N=100,000, M=3: 19.00 MB read + 574.31 MB written for 635.79 MB of tiles).
 # The kernel's reads (prefix sets, bucket index, keys) and writes (tiles) grow
 # with the tiles it writes, so the bench scales it by the timed workload's
 # tile bytes. It is reported only while the kernel sources are the ones it
 # was measured on.
-DOM_TRAFFIC_PER_TILE_BYTE = (19_124_992 + 574_383_616) / 635_785_216
-DOM_TRAFFIC_SOURCES_SHA1 = "27319f283fc8da3e9c3e0a1b7c0abd8c98a28d0c"
+DOM_TRAFFIC_PER_TILE_BYTE = (18_997_504 + 574_313_984) / 635_785_216
+DOM_TRAFFIC_SOURCES_SHA1 = "2fef57b62605552946187e6fbebff2dd5eb9c084"
 DOM_SOURCES = ("k_dominance.cu", "emo_kernels.cuh", "emo_internal.cuh")
 
 
