@@ -2,12 +2,16 @@
 //   p = 1[c = 0];  loop { r[p] = k;  d_j = sum_i p_i D_ij;  c -= d + p;  k++ }
 // with c the number of dominators of each point (column sums of D).
 //
-// One cooperative launch per call. Each CTA of a problem's group owns whole
-// column blocks (1024 sorted points) and their counts; blocks are dealt in
-// descending order in a snake over the CTAs (block cb has about cb + 1 units
-// of work per front, so the snake keeps the largest CTA load within a few
-// blocks of the mean). Per front, the CTA stages the members whose rows reach
-// its blocks in shared memory; for each owned block every warp copies the
+// One cooperative launch per call. Per front, the CTAs of a problem's group
+// take whole column blocks (1024 sorted points; their counts live in global
+// memory): block cb has about cb + 1 units of work per front, so with more
+// than two blocks per CTA of a group of at least 64 CTAs they come from a
+// counter, the last block first, and the CTAs finish the front together;
+// otherwise each CTA takes the blocks dealt to it in a snake over the CTAs
+// (descending). For each
+// block the CTA stages the members whose rows reach it in shared memory (a
+// prefix of the front's list in block order, so one staging serves the
+// smaller blocks the CTA takes next); every warp copies the
 // 128-byte row segments of 32 members at a time into its own ring of
 // shared-memory stages with cp.async (the next batch in flight while one
 // is counted), then adds the words into per-lane Harley-Seal bit-sliced
@@ -157,10 +161,11 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
     }
     if (!group_sync(d.sc, g.size, budget)) return;
 
-    // the largest owned block is the first one dealt
-    const int last_cb = peel_block(0, g.rank, g.size, ncb);
     int64_t prev_total = 0, total = ld_volatile(&d.sc->ranked);
     int k = 0;
+    __shared__ int s_item;
+    // (a counter round trip per block pays only across many CTAs)
+    const bool dynamic = g.size >= 64 && ncb > 2 * g.size;
     while (total < target) {
         if (total == prev_total || k >= n2) {  // empty front before the target: inconsistent counts
             if (tid == 0) set_status(d.sc, EMO_ERR_INVALID_ARG);
@@ -171,42 +176,71 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
         const int32_t* frn = d.front_n + (int64_t)cur * ncb;
         int32_t* fw = d.front + (int64_t)nxt * n2p;
         int32_t* fwn = d.front_n + (int64_t)nxt * ncb;
+        // the next front's block counter (every CTA left this one's loop
+        // before the last barrier)
+        if (g.rank == 0 && tid == 0) d.wcnt[nxt] = 0;
 
-        // prefix of the member counts of every column block up to the last owned one
-        if (last_cb >= 0) {
+        // prefix of the member counts of every column block
+        {
             int run = 0;
-            for (int base = 0; base <= last_cb; base += blockDim.x) {
+            for (int base = 0; base < ncb; base += blockDim.x) {
                 const int c = base + tid;
-                const int v = c <= last_cb ? __ldcg(&frn[c]) : 0;
+                const int v = c < ncb ? __ldcg(&frn[c]) : 0;
                 int tot;
                 const int pre = block_exclusive_scan<kCoopThreads>(v, s_warp, tot);
-                if (c <= last_cb) s_pref[c] = run + pre;
+                if (c < ncb) s_pref[c] = run + pre;
                 run += tot;
                 __syncthreads();
             }
-            if (tid == 0) s_pref[last_cb + 1] = run;
+            if (tid == 0) s_pref[ncb] = run;
             __syncthreads();
         }
-        const int nall = last_cb >= 0 ? s_pref[last_cb + 1] : 0;  // members reaching the last owned block
 
-        for (int m0 = 0; m0 < nall; m0 += kPeelChunk) {
-            const int mc = min(kPeelChunk, nall - m0);
-            __syncthreads();
-            // stage the (encoded) members m0 .. m0 + mc in block order: warp w
-            // copies the lists of blocks w, w + NW, ... with async 4-byte copies
-            for (int c = warp; c <= last_cb; c += NW) {
-                const int b0 = s_pref[c], lo = max(b0, m0), hi = min(s_pref[c + 1], m0 + mc);
-                for (int o = lo + lane; o < hi; o += 32)
-                    cp_async4(smem_u32(s_mem + (o - m0)), fr + (int64_t)c * kColBlock + (o - b0));
-            }
-            cp_async_commit();
-            cp_async_wait<0>();
-            __syncthreads();
-            for (int r = 0;; ++r) {
-                const int cb = peel_block(r, g.rank, g.size, ncb);
+        // With more than two column blocks per CTA over a group of at least
+        // 64 CTAs, blocks are taken from a counter, the last (heaviest)
+        // first, so that the CTAs finish the front together; otherwise each
+        // CTA takes its blocks of the snake
+        // (no counter round trip per block). Either way a CTA visits its
+        // blocks in descending order: the members reaching block cb are the
+        // first s_pref[cb + 1] of the list in block order, so a chunk staged
+        // for one block serves every smaller block the CTA takes after it.
+        int staged_m0 = -1, staged_mc = 0;
+        for (int round = 0;; ++round) {
+            int cb;
+            if (dynamic) {
+                if (tid == 0) s_item = atomicAdd(&d.wcnt[cur], 1);
+                __syncthreads();
+                const int item = s_item;
+                __syncthreads();  // every thread has read s_item
+                if (item >= ncb) break;
+                cb = ncb - 1 - item;
+            } else {
+                cb = peel_block(round, g.rank, g.size, ncb);
                 if (cb < 0) break;
-                const int nmem = min(mc, s_pref[cb + 1] - m0);  // staged members reaching cb
-                if (nmem <= 0) continue;
+            }
+            const int nreach = s_pref[cb + 1];  // members whose rows reach cb
+            if (nreach == 0) {
+                if (tid == 0) fwn[cb] = 0;
+                continue;
+            }
+            for (int m0 = 0; m0 < nreach; m0 += kPeelChunk) {
+                const int nmem = min(kPeelChunk, nreach - m0);
+                if (staged_m0 != m0 || staged_mc < nmem) {
+                    // stage the (encoded) members m0 .. m0 + nmem in block order:
+                    // warp w copies the lists of blocks w, w + NW, ... with async
+                    // 4-byte copies
+                    __syncthreads();
+                    for (int c = warp; c <= cb; c += NW) {
+                        const int b0 = s_pref[c], lo = max(b0, m0), hi = min(s_pref[c + 1], m0 + nmem);
+                        for (int o = lo + lane; o < hi; o += 32)
+                            cp_async4(smem_u32(s_mem + (o - m0)), fr + (int64_t)c * kColBlock + (o - b0));
+                    }
+                    cp_async_commit();
+                    cp_async_wait<0>();
+                    __syncthreads();
+                    staged_m0 = m0;
+                    staged_mc = nmem;
+                }
                 // new members of one block may arrive over several member chunks:
                 // append after those found in the earlier chunks of this front
                 if (tid == 0) s_base = s_newn = m0 == 0 ? 0 : fwn[cb];
@@ -282,13 +316,6 @@ __global__ void __launch_bounds__(kCoopThreads, 1) k_peel(Plan* plan)
                 }
             }
         }
-        // blocks that received no member in this front still need their count of new members
-        if (tid == 0)
-            for (int r = 0;; ++r) {
-                const int cb = peel_block(r, g.rank, g.size, ncb);
-                if (cb < 0) break;
-                if (nall == 0 || s_pref[cb + 1] == 0) fwn[cb] = 0;
-            }
         if (!group_sync(d.sc, g.size, budget)) return;
         prev_total = total;
         total = ld_volatile(&d.sc->ranked);
